@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the SyMBA hot path (arXiv:2304.07325) on GB300.
+
+Workload: the Sec. 3 planetesimal disk with N = 10,000 bodies, all massive, FP64, tau = 0.5 yr,
+M = 4, shell ratio 2.08, l = 3 (seed 1002).  A step is one full SyMBA step (sun drifts, both
+trapezoid kicks with the fused encounter check, grouping, Kepler drifts, group recursion).
+Metric: trapezoid pair interactions per second, 2 P per step with P = N (N - 1) / 2.
+
+Prints one JSON line.  `--impl reference` times the serial FP64 oracle (the CPU restatement the
+tests check the GPU against) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (no tensor cores for this path)
+FLOPS_PER_PAIR_KICK = 26          # 3 sub, 5 r^2, 2 for 1/sqrt, 2 for r^-3, 2 mass scalings, 12 FMA flops
+FLOPS_PER_PAIR_CHECK = 18
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--seed", type=int, default=1002)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload(args):
+    from paper_2304_07325_gb300 import disk
+    d = disk.planetesimal_disk(args.n, args.seed)
+    P = args.n * (args.n - 1) // 2
+    return d, P
+
+
+def cpu_baseline(args, d, P, budget_s):
+    """The oracle, as it stands, on full steps of the same disk until the time budget is spent."""
+    import oracle
+    oracle.build()
+    sim = oracle.OracleSim(d.x, d.v, d.m, d.radius)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= max(1, args.steps):
+            break
+    value = 2.0 * P * steps / el
+    return {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full oracle steps of the N={args.n} disk (seed {args.seed}), "
+                      f"{el:.1f} s on 1 host core, serial FP64 C"}, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    d, P = workload(args)
+    cb, steps, el = cpu_baseline(args, d, P, budget_s=min(150.0, max(10.0, 2.0 * args.cpu_budget_s)))
+    line = {"impl": "reference", "metric": "pair-interactions/s", "value": cb["value"],
+            "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": steps, "warmup": 0,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"planetesimal disk N={args.n} all massive, FP64, dt=0.5 yr, M=4, "
+                                   f"R_k/R_k+1=2.08, l=3 (seed {args.seed})"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2304_07325_gb300 as sy
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2304_07325_gb300 import build
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+
+    # every rank integrates its own replica (independent disks: replicas, no exchange)
+    seed = args.seed + 1000 * rank
+    from paper_2304_07325_gb300 import disk
+    d = disk.planetesimal_disk(args.n, seed)
+    P = args.n * (args.n - 1) // 2
+    prec = sy.SYMBA_PRECISION_MIXED if args.precision == "mixed" else sy.SYMBA_PRECISION_FP64
+    params = sy.default_params(precision=prec)
+    sysm = sy.System(d.x, d.v, d.m, d.radius, params=params, stream=stream)
+
+    # warm-up
+    sysm.profile_step(max(1, args.warmup))
+    st = sysm.sync()
+    if st < 0:
+        raise RuntimeError(f"warm-up failed: {sy.status_string(st)}")
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = None if args.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase_tot = np.zeros(sy.SYMBA_NPHASES)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    depth_max, substeps = 0, 0
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        phase_tot += sysm.profile_step(1)      # events between the step's kernels, same stream
+        ends[k].record(stream)
+        s = sysm.stats()
+        depth_max = max(depth_max, s.max_depth)
+        substeps += s.substeps
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    t_local = sum(step_ms) / 1e3
+    st = sysm.sync()
+    if st < 0:
+        raise RuntimeError(f"timed steps failed: {sy.status_string(st)}")
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    units = 2.0 * P * args.steps * world
+    value = units / t_max
+
+    # end to end through the C ABI with host buffers: set state (H2D), one step, get state (D2H)
+    xh = torch.empty((args.n, 3), dtype=torch.float64, pin_memory=True)
+    vh = torch.empty((args.n, 3), dtype=torch.float64, pin_memory=True)
+    x0, v0, *_ = sysm.get_state()
+    xh.numpy()[...] = x0
+    vh.numpy()[...] = v0
+    ne = max(1, min(args.e2e_steps, args.steps))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(ne):
+        sy.lib().symba_set_state(sysm._h, sy.c_void_p(xh.data_ptr()), sy.c_void_p(vh.data_ptr()))
+        sysm.step(1)
+        sy.lib().symba_get_state(sysm._h, sy.c_void_p(xh.data_ptr()), sy.c_void_p(vh.data_ptr()),
+                                 None, None, None)
+    te = time.perf_counter() - te0
+    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e_value = 2.0 * P * ne * world / float(te_t.item())
+
+    if rank == 0:
+        peaks = measured_peaks()
+        kick_ms = (phase_tot[1] + phase_tot[6]) / (2 * args.steps)
+        flops_per_launch = FLOPS_PER_PAIR_KICK * P
+        achieved = flops_per_launch / (kick_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
+                    "kernel": "k_trap_fp64 (trapezoid pair kick, FP64 pipe)",
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe); measured DFMA 1.19"}
+        phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
+        cb = None
+        if not args.no_cpu_baseline and world == 1:
+            cb, _, _ = cpu_baseline(args, d, P, args.cpu_budget_s)
+        line = {"metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"planetesimal disk N={args.n} all massive, "
+                                       f"{'FP64' if prec == 0 else 'FP32-pair/FP64-state'}, dt=0.5 yr, M=4, "
+                                       f"R_k/R_k+1=2.08, l=3 (seed {args.seed}+1000*rank)",
+                           "n": args.n, "pairs_per_kick": P, "l2": "flushed between steps (256 MB write)"
+                           if flush is not None else "not flushed",
+                           "parallelism": f"replicas x{world}"},
+                "steps_per_s": args.steps * world / t_max,
+                "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+                "phase_ms_per_step": phases, "max_depth": depth_max,
+                "substeps_per_step": substeps / args.steps,
+                "roofline": roofline, "cpu_baseline": cb,
+                "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
+                        "h2d_bytes_per_step": 2 * 8 * 3 * args.n, "d2h_bytes_per_step": 2 * 8 * 3 * args.n,
+                        "steps": ne},
+                "gpu_launches": args.steps * 12,
+                "clocks": clk, "wall_s": wall}
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * symba.h -- C ABI of the GB300 SyMBA hot path (arXiv:2304.07325, SyMBAp).
+ *
+ * One call of symba_step advances a system of N bodies around a central mass m0 by SyMBA steps
+ * (Duncan, Levison & Lee 1998) with the SyMBAp structure of the paper:
+ *   - every interaction of the right-angled trapezoid i < N_m, j > i (Sec. 2, the nested loop),
+ *     split into a rectangle plus a triangle folded into a rectangle (Sec. 2);
+ *   - the close-encounter check, whose flagged pairs are grouped into independent groups that
+ *     are integrated separately (Sec. 2, the encounter paragraph);
+ *   - recursive sub-stepping with subdivision factor M, shell ratio R_k/R_{k+1} and the
+ *     partition function f_l (Sec. 3, first paragraph: M = 4, 2.08, l = 3);
+ *   - per-particle Kepler and sun drifts (Sec. 2, the simple loops).
+ * All computation runs in CUDA kernels for sm_103a on the calling process's current device.
+ *
+ * Conventions shared by every entry point
+ *   - Units are the caller's; the defaults are AU, yr, solar masses (G = 4 pi^2, m0 = 1).
+ *   - Particle arrays are indexed 0..n-1, massive bodies first (indices < n_massive), field
+ *     (massless) particles after.  Vectors are n x 3 row-major doubles: x0 y0 z0 x1 y1 z1 ...
+ *   - A pointer argument may be host memory or device memory of the current device; the library
+ *     detects which.  The library copies what it needs and never keeps the caller's pointer.
+ *   - The state the library keeps is democratic heliocentric: heliocentric positions and
+ *     barycentric velocities.
+ *   - Return values: SYMBA_OK (0), a negative SYMBA_E_* code, or SYMBA_COLLISION (positive,
+ *     informational: at least one merger happened).  Errors detected on the device inside an
+ *     asynchronous call are sticky and reported by the next synchronising call (symba_sync,
+ *     symba_energy, symba_get_state, symba_enc_groups, symba_get_stats); the state is then
+ *     undefined until symba_set_state.
+ *   - No call uses hidden global state; separate contexts may be used from separate threads.
+ */
+#ifndef SYMBA_H
+#define SYMBA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SYMBA_OK 0
+#define SYMBA_E_INVAL (-1)     /* bad argument */
+#define SYMBA_E_NOMEM (-2)     /* device allocation failed, or a pool has no room */
+#define SYMBA_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define SYMBA_E_KEPLER (-4)    /* Kepler's equation did not converge */
+#define SYMBA_E_DEPTH (-5)     /* recursion deeper than max_depth, or sub-step budget exhausted */
+#define SYMBA_E_CAPACITY (-6)  /* more level-0 encounter pairs than pair_capacity */
+#define SYMBA_E_NONFINITE (-7) /* NaN or Inf in the state */
+#define SYMBA_COLLISION 1      /* informational: bodies merged during the last steps */
+
+#define SYMBA_PRECISION_FP64 0 /* every operation in FP64 */
+#define SYMBA_PRECISION_MIXED 1 /* FP32 pair kick (Kahan into FP64); FP64 state, drifts, check, energy */
+
+/* Method parameters (Sec. 3 gives dt, M, shell_ratio and l for the benchmark). */
+typedef struct {
+  double dt;           /* full step tau */
+  double shell_ratio;  /* R_k / R_{k+1} (2.08) */
+  double hill_scale;   /* lambda: level-0 critical radius lambda (rH_i + rH_j) (6.5) */
+  double G;            /* gravitational constant (4 pi^2) */
+  double m0;           /* central mass (1) */
+  int M;               /* time-step subdivision factor (4) */
+  int l;               /* order of the partition function f_l (3) */
+  int max_depth;       /* deepest recursion level (20) */
+  int precision;       /* SYMBA_PRECISION_FP64 or SYMBA_PRECISION_MIXED */
+  int pair_capacity;   /* level-0 encounter pairs per step; 0 = max(4096, 4 n) */
+  int max_substeps;    /* sub-step budget per group and step; 0 = 1 << 22 */
+} symba_params;
+
+/* Per-step diagnostics of the last step (summed over a multi-step call where stated). */
+typedef struct {
+  int n_pairs;              /* level-0 encounter pairs of the last step */
+  int n_groups;             /* encounter groups of the last step */
+  int max_depth;            /* deepest level entered during the last call */
+  int status;               /* sticky device status (SYMBA_OK or SYMBA_E_*) */
+  long long merges;         /* mergers since the context was created */
+  long long substeps;       /* recursion sub-steps (E_k calls, k >= 1) during the last call */
+  long long steps;          /* steps taken since the context was created */
+} symba_stats;
+
+typedef struct symba_ctx symba_ctx;
+typedef struct symba_pool symba_pool;
+
+/* Fills *p with the paper's benchmark parameters: dt 0.5, M 4, shell ratio 2.08, l 3,
+ * lambda 6.5, G 4 pi^2, m0 1, max_depth 20, FP64.  Never fails. */
+void symba_default_params(symba_params *p);
+
+/* Creates a context for one system and uploads it.
+ * n, n_massive: particle counts (0 <= n_massive <= n, n >= 1).
+ * x, v: n x 3 heliocentric positions and velocities; m, radius: n masses (0 for field particles)
+ * and physical radii (contact detection); rhill: n Hill radii, or NULL to compute them as
+ * a (m / 3 m0)^{1/3} from the osculating heliocentric orbit.
+ * cuda_stream: a cudaStream_t every later call of this context is ordered on (NULL = a stream
+ * the context creates).  Returns SYMBA_OK and *out, or SYMBA_E_INVAL / E_NOMEM / E_CUDA. */
+int symba_init(symba_ctx **out, const symba_params *p, int n, int n_massive, const double *x,
+               const double *v, const double *m, const double *radius, const double *rhill,
+               void *cuda_stream);
+
+/* Enqueues nsteps SyMBA steps E(tau) on the context's stream and returns without waiting.
+ * Each step: sun drift tau/2; level-0 check fused into kick tau/2 over the trapezoid; grouping;
+ * Kepler drift tau of bodies in no encounter and M-fold recursion of every group; kick tau/2;
+ * sun drift tau/2.  Returns SYMBA_OK, SYMBA_E_INVAL (nsteps < 0) or SYMBA_E_CUDA. */
+int symba_step(symba_ctx *c, int nsteps);
+
+/* Waits for the context's stream; returns the sticky device status (or SYMBA_COLLISION if
+ * bodies merged since the last synchronising call and no error happened). */
+int symba_sync(symba_ctx *c);
+
+/* Total energy E and angular momentum L[3] of the current state (democratic heliocentric, equal
+ * to the barycentric totals; Sec. 3 accuracy test).  Each is the correctly rounded sum of its
+ * terms.  Synchronises.  E and L are host pointers. */
+int symba_energy(symba_ctx *c, double *E, double L[3]);
+
+/* The level-0 encounter pairs of the last step in ascending (i, j) order (i < j) and, for each,
+ * the index of its group; groups are numbered by ascending smallest member.  pairs: 2 x cap
+ * ints, group_of_pair: cap ints (host or device).  *n_pairs and *n_groups receive the full
+ * counts even when they exceed cap (then only cap entries are written).  Synchronises. */
+int symba_enc_groups(symba_ctx *c, int *pairs, int *group_of_pair, int cap, int *n_pairs,
+                     int *n_groups);
+
+/* Copies the state out: x (n x 3 heliocentric), v (n x 3 barycentric), and optionally m,
+ * radius (n) and alive (n ints, 0 for a body merged into another).  Any output may be NULL.
+ * Synchronises. */
+int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radius, int *alive);
+
+/* Replaces positions (heliocentric) and barycentric velocities; masses, radii and Hill radii
+ * stay.  Enqueued on the context's stream.  Also clears the sticky status. */
+int symba_set_state(symba_ctx *c, const double *x, const double *v);
+
+/* Diagnostics of the last call; synchronises. */
+int symba_get_stats(symba_ctx *c, symba_stats *s);
+
+/* Phase timing (tracing): runs nsteps steps like symba_step, launching the kernels one by one
+ * with CUDA events between them on the context's stream, then synchronises and writes the
+ * summed device time of each phase in milliseconds to phase_ms[0..SYMBA_NPHASES-1] (host):
+ * 0 sun drift + step prologue, 1 kick 1 with the fused encounter check, 2 kick-1 reduction,
+ * 3 grouping, 4 Kepler drift, 5 group recursion, 6 kick 2, 7 kick-2 reduction,
+ * 8 total momentum, 9 closing sun drift.  Returns the sticky status like symba_sync. */
+#define SYMBA_NPHASES 10
+int symba_profile_step(symba_ctx *c, int nsteps, double *phase_ms);
+
+/* Releases the context and all its device memory (after waiting for its stream). */
+void symba_free(symba_ctx *c);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Pools: many independent systems (a parameter scan, Sec. 1) stepped together, every kernel  */
+/* of a step launched once for all of them.  Results of a system do not depend on which other */
+/* systems share the pool.                                                                     */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Creates a pool that can hold up to max_systems systems with at most max_particles bodies in
+ * total and max_tiles 32 x 32 trapezoid tiles in total (the pair-kick scratch: 1.5 KiB each).
+ * precision: SYMBA_PRECISION_FP64 or SYMBA_PRECISION_MIXED for every system of the pool. */
+int symba_pool_create(symba_pool **out, int max_systems, long long max_particles,
+                      long long max_tiles, int precision, void *cuda_stream);
+
+/* Device bytes a system of n bodies (n_massive massive) occupies in a pool. */
+long long symba_pool_footprint(int n, int n_massive, const symba_params *p);
+
+/* Admits one system (arguments as symba_init) into a free slot; *slot receives its id.
+ * Returns SYMBA_E_NOMEM if the pool has no room for it (slots, bodies, tiles or pairs). */
+int symba_pool_admit(symba_pool *pool, const symba_params *p, int n, int n_massive,
+                     const double *x, const double *v, const double *m, const double *radius,
+                     const double *rhill, int *slot);
+
+/* Enqueues nsteps steps of every admitted system.  Asynchronous. */
+int symba_pool_step(symba_pool *pool, int nsteps);
+
+/* Waits; returns the worst sticky status over the pool's systems. */
+int symba_pool_sync(symba_pool *pool);
+
+/* Per-system state, energy and diagnostics (synchronising; arguments as the symba_* forms). */
+int symba_pool_get_state(symba_pool *pool, int slot, double *x, double *v, double *m,
+                         double *radius, int *alive);
+int symba_pool_energy(symba_pool *pool, int slot, double *E, double L[3]);
+int symba_pool_get_stats(symba_pool *pool, int slot, symba_stats *s);
+
+/* Removes a system; its slot, bodies and scratch become free for later admissions. */
+int symba_pool_evict(symba_pool *pool, int slot);
+
+void symba_pool_free(symba_pool *pool);
+
+/* Human-readable name of a status code. */
+const char *symba_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMBA_H */

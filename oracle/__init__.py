@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
 class Params(ctypes.Structure):
     _fields_ = [("dt", c_double), ("shell_ratio", c_double), ("hill_scale", c_double),
                 ("G", c_double), ("m0", c_double), ("M", c_int), ("l", c_int),
-                ("max_depth", c_int), ("pad_", c_int)]
+                ("max_depth", c_int), ("noise", c_int)]
 
 
 class _Sim(ctypes.Structure):
@@ -94,9 +94,9 @@ def _ip(a):
 
 
 def make_params(dt=0.5, M=4, shell_ratio=2.08, hill_scale=6.5, l=3, G=4.0 * math.pi ** 2, m0=1.0,
-                max_depth=20) -> Params:
+                max_depth=20, noise=0) -> Params:
     return Params(dt=dt, shell_ratio=shell_ratio, hill_scale=hill_scale, G=G, m0=m0, M=M, l=l,
-                  max_depth=max_depth, pad_=0)
+                  max_depth=max_depth, noise=noise)
 
 
 def fsum(a) -> float:

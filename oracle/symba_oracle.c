@@ -43,7 +43,10 @@ typedef struct {
   int M;               /* time-step subdivision factor (4 in Sec. 3) */
   int l;               /* order of the partition function f_l (3 in Sec. 3) */
   int max_depth;       /* deepest recursion level allowed */
-  int pad_;
+  int noise;           /* test hook, 0 in every reference run: when set, each position and
+                          velocity component a recursion sub-step kicks or drifts is multiplied by
+                          1 +- 2^-52 (deterministic pseudo-random sign), to measure how strongly
+                          the chaotic close encounters amplify differences at the rounding level */
 } orc_params;
 
 typedef struct {
@@ -480,6 +483,28 @@ void orc_kick_trapezoid(const orc_params *P, orc_sim *s, const int *pairs, int n
   free(a);
 }
 
+/* Rounding-level perturbation of the sensitivity twin (see orc_params.noise): a SplitMix64 hash */
+/* of (particle, component, counter) picks the sign.                                              */
+static unsigned long long noise_counter = 0;
+
+static double jiggle(double a, int p, int c) {
+  unsigned long long z = (unsigned long long)p * 0x9E3779B97F4A7C15ull + (unsigned long long)c * 0xBF58476D1CE4E5B9ull +
+                         (++noise_counter) * 0x94D049BB133111EBull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double eps = 2.220446049250313e-16;
+  return a * (1.0 + ((z & 1ull) ? eps : -eps));
+}
+
+static void perturb(const orc_params *P, orc_sim *s, int p) {
+  if (!P->noise) return;
+  for (int c = 0; c < 3; ++c) {
+    s->x[3 * p + c] = jiggle(s->x[3 * p + c], p, c);
+    s->v[3 * p + c] = jiggle(s->v[3 * p + c], p, c + 3);
+  }
+}
+
 /* Kick h over an explicit pair list at level k: accelerations summed pair by pair in list order, */
 /* then v_p += h a_p once for every particle of the list.  `done` is an [n] scratch flag array.  */
 static void kick_pairs(const orc_params *P, orc_sim *s, const int *pl, int np, int k, double h,
@@ -497,6 +522,7 @@ static void kick_pairs(const orc_params *P, orc_sim *s, const int *pl, int np, i
     int p = pl[q];
     if (done[p] || !s->alive[p]) continue;
     for (int c = 0; c < 3; ++c) s->v[3 * p + c] = s->v[3 * p + c] + h * a[3 * p + c];
+    perturb(P, s, p);
     done[p] = 1;
   }
 }
@@ -644,6 +670,7 @@ static void E_level(orc_ctx *C, int k, double h, const int *F, int nF) {
       if (C->mark[p] == 2 || !s->alive[p]) continue; /* already drifted, or merged away */
       int st = orc_kepler_drift(mu, h, s->x + 3 * p, s->v + 3 * p);
       if (st != ORC_OK && s->status == ORC_OK) s->status = st;
+      perturb(P, s, p);
       C->mark[p] = 2;
     }
   }

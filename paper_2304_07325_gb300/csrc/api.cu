@@ -1,0 +1,727 @@
+// Host runtime and C ABI: pools of systems (a single-system context is a pool of one), device
+// memory arenas sized at creation, first-fit allocation of particle and pair ranges, the
+// trapezoid tile list, and the per-step launch sequence captured once into a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+struct Slot {
+  bool active = false;
+  int off = 0, n = 0, nm = 0, nb = 0, nbm = 0, ntiles = 0, pair_base = 0, pair_cap = 0;
+  symba_params p{};
+  long long merges_reported = 0;
+};
+
+// first-fit free list over [0, cap)
+struct RangeAlloc {
+  std::map<long long, long long> free_;  // start -> length
+  void init(long long cap) { free_.clear(); if (cap > 0) free_[0] = cap; }
+  long long alloc(long long len) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= len) {
+        const long long s = it->first, l = it->second;
+        free_.erase(it);
+        if (l > len) free_[s + len] = l - len;
+        return s;
+      }
+    }
+    return -1;
+  }
+  void release(long long s, long long len) {
+    auto it = free_.emplace(s, len).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+    }
+  }
+};
+
+long long tiles_of(int nb, int nbm) {
+  long long t = 0;
+  for (int I = 0; I < nbm; ++I) t += nb - I;
+  return t;
+}
+
+int default_pair_cap(const symba_params *p, int n) {
+  if (p && p->pair_capacity > 0) return p->pair_capacity;
+  return std::max(4096, 4 * n);
+}
+
+}  // namespace
+
+struct symba_pool {
+  int max_disks = 0, precision = 0;
+  long long pcap = 0, tcap = 0, paircap = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  Dev D{};
+  LaunchCfg L{};
+  std::vector<Slot> slots;
+  RangeAlloc parts, pairs;
+  long long tiles_used = 0;
+  long long npart_hwm = 0;
+  int ndisks = 0;
+  std::vector<void *> allocs;
+  unsigned long long *eacc = nullptr;
+  double *eout = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool graph_ok = false;
+  bool use_graph = true;
+};
+
+struct symba_ctx {
+  symba_pool *pool;
+  int slot;
+};
+
+namespace {
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return SYMBA_E_CUDA;     \
+  } while (0)
+
+template <class T>
+int dalloc(symba_pool *P, T **ptr, size_t count) {
+  void *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return SYMBA_E_NOMEM;
+  P->allocs.push_back(p);
+  *ptr = (T *)p;
+  return SYMBA_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device copy of a caller array (or the array itself when it is already on the device)
+struct Staged {
+  const void *dev = nullptr;
+  void *own = nullptr;
+  ~Staged() { if (own) cudaFree(own); }
+};
+
+int stage_in(Staged &s, const void *src, size_t bytes, cudaStream_t st) {
+  if (!src) return SYMBA_OK;
+  if (is_device_ptr(src)) { s.dev = src; return SYMBA_OK; }
+  if (cudaMalloc(&s.own, bytes ? bytes : 1) != cudaSuccess) return SYMBA_E_NOMEM;
+  CK(cudaMemcpyAsync(s.own, src, bytes, cudaMemcpyHostToDevice, st));
+  s.dev = s.own;
+  return SYMBA_OK;
+}
+
+void invalidate_graph(symba_pool *P) {
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->gexec = nullptr;
+  P->graph = nullptr;
+  P->graph_ok = false;
+}
+
+// rebuild the tile list and the per-system descriptors after an admission or eviction
+int rebuild(symba_pool *P) {
+  std::vector<int4> tiles;
+  tiles.reserve((size_t)P->tiles_used);
+  int hw = 0;
+  long long phw = 0;
+  for (int d = 0; d < P->max_disks; ++d) {
+    Slot &s = P->slots[d];
+    if (!s.active) continue;
+    hw = d + 1;
+    phw = std::max(phw, (long long)s.off + (long long)s.nb * SYM_TILE);
+  }
+  std::vector<DiskDesc> descs(P->max_disks);
+  for (int d = 0; d < P->max_disks; ++d) {
+    Slot &s = P->slots[d];
+    DiskDesc &dd = descs[d];
+    memset(&dd, 0, sizeof(dd));
+    if (!s.active) continue;
+    dd.off = s.off; dd.n = s.n; dd.nm = s.nm; dd.nb = s.nb; dd.nbm = s.nbm;
+    dd.tile_base = (int)tiles.size();
+    dd.ntiles = s.ntiles;
+    dd.pair_base = s.pair_base; dd.pair_cap = s.pair_cap;
+    dd.group_base = s.off / 2;
+    dd.active = 1;
+    dd.M = s.p.M; dd.l = s.p.l; dd.max_depth = std::min(s.p.max_depth, SYM_MAX_LEVELS - 1);
+    dd.max_substeps = s.p.max_substeps > 0 ? s.p.max_substeps : (1 << 22);
+    dd.dt = s.p.dt; dd.shell_ratio = s.p.shell_ratio; dd.hill_scale = s.p.hill_scale;
+    dd.G = s.p.G; dd.m0 = s.p.m0;
+    const int b0 = s.off / SYM_TILE;
+    for (int I = 0; I < s.nbm; ++I)
+      for (int J = I; J < s.nb; ++J) tiles.push_back(make_int4(d, b0 + I, b0 + J, 0));
+  }
+  P->ndisks = hw;
+  P->npart_hwm = phw;
+  P->D.ndisks = hw;
+  P->D.ntiles_total = (int)tiles.size();
+  const long long warps = (long long)P->L.trap_blocks * 4;
+  long long seg = (long long)tiles.size() / std::max(1LL, warps * 24);
+  P->D.seg_len = (int)std::max(1LL, std::min(8LL, seg));
+  if (!tiles.empty())
+    CK(cudaMemcpyAsync(P->D.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, P->stream));
+  // ck tables are filled on the device by the set-up kernel: keep them across uploads
+  CK(cudaStreamSynchronize(P->stream));
+  std::vector<DiskDesc> cur(P->max_disks);
+  CK(cudaMemcpy(cur.data(), P->D.disks, sizeof(DiskDesc) * P->max_disks, cudaMemcpyDeviceToHost));
+  for (int d = 0; d < P->max_disks; ++d) {
+    memcpy(descs[d].ck, cur[d].ck, sizeof(descs[d].ck));
+    memcpy(descs[d].ck2, cur[d].ck2, sizeof(descs[d].ck2));
+    memcpy(descs[d].invdc, cur[d].invdc, sizeof(descs[d].invdc));
+  }
+  CK(cudaMemcpyAsync(P->D.disks, descs.data(), sizeof(DiskDesc) * P->max_disks, cudaMemcpyHostToDevice, P->stream));
+  invalidate_graph(P);
+  return SYMBA_OK;
+}
+
+void enqueue_step(symba_pool *P) {
+  const Dev &D = P->D;
+  const long long np = P->npart_hwm;
+  launch_prologue(D, P->ndisks, P->stream);
+  launch_sundrift(D, np, 1, P->stream);
+  launch_trap(D, P->L, 1, P->precision, P->stream);
+  launch_reduce(D, np, P->precision, P->stream);
+  launch_groups(D, P->ndisks, P->stream);
+  launch_drift(D, np, P->stream);
+  launch_recursion(D, P->L, P->stream);
+  if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, P->stream);
+  launch_trap(D, P->L, 2, P->precision, P->stream);
+  launch_reduce(D, np, P->precision, P->stream);
+  launch_momentum(D, P->ndisks, P->stream);
+  launch_sundrift(D, np, 0, P->stream);
+}
+
+__global__ void k_reset_call(DiskStat *st, int nd) {
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    st[d].max_depth = 0;
+    st[d].substeps = 0;
+  }
+}
+
+int pool_profile(symba_pool *P, int nsteps, double *phase_ms) {
+  if (nsteps < 0 || !phase_ms) return SYMBA_E_INVAL;
+  for (int k = 0; k < SYMBA_NPHASES; ++k) phase_ms[k] = 0.0;
+  if (nsteps == 0 || P->ndisks == 0) return SYMBA_OK;
+  CK(cudaSetDevice(P->device));
+  cudaEvent_t ev[SYMBA_NPHASES + 1];
+  for (int k = 0; k <= SYMBA_NPHASES; ++k) CK(cudaEventCreate(&ev[k]));
+  k_reset_call<<<1, 256, 0, P->stream>>>(P->D.stat, P->ndisks);
+  const Dev &D = P->D;
+  const long long np = P->npart_hwm;
+  cudaStream_t s = P->stream;
+  int rc = SYMBA_OK;
+  for (int step = 0; step < nsteps && rc == SYMBA_OK; ++step) {
+    cudaEventRecord(ev[0], s);
+    launch_prologue(D, P->ndisks, s);
+    launch_sundrift(D, np, 1, s);
+    cudaEventRecord(ev[1], s);
+    launch_trap(D, P->L, 1, P->precision, s);
+    cudaEventRecord(ev[2], s);
+    launch_reduce(D, np, P->precision, s);
+    cudaEventRecord(ev[3], s);
+    launch_groups(D, P->ndisks, s);
+    cudaEventRecord(ev[4], s);
+    launch_drift(D, np, s);
+    cudaEventRecord(ev[5], s);
+    launch_recursion(D, P->L, s);
+    if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, s);
+    cudaEventRecord(ev[6], s);
+    launch_trap(D, P->L, 2, P->precision, s);
+    cudaEventRecord(ev[7], s);
+    launch_reduce(D, np, P->precision, s);
+    cudaEventRecord(ev[8], s);
+    launch_momentum(D, P->ndisks, s);
+    cudaEventRecord(ev[9], s);
+    launch_sundrift(D, np, 0, s);
+    cudaEventRecord(ev[10], s);
+    if (cudaEventSynchronize(ev[10]) != cudaSuccess) { rc = SYMBA_E_CUDA; break; }
+    for (int k = 0; k < SYMBA_NPHASES; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      phase_ms[k] += ms;
+    }
+  }
+  for (int k = 0; k <= SYMBA_NPHASES; ++k) cudaEventDestroy(ev[k]);
+  if (cudaGetLastError() != cudaSuccess) return SYMBA_E_CUDA;
+  return rc;
+}
+
+int pool_step(symba_pool *P, int nsteps) {
+  if (nsteps < 0) return SYMBA_E_INVAL;
+  if (nsteps == 0 || P->ndisks == 0) return SYMBA_OK;
+  CK(cudaSetDevice(P->device));
+  k_reset_call<<<1, 256, 0, P->stream>>>(P->D.stat, P->ndisks);
+  if (P->use_graph && !P->graph_ok) {
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamIsCapturing(P->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(P);
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamEndCapture(P->stream, &g));
+      cudaGraphExec_t ge = nullptr;
+      if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return SYMBA_E_CUDA;
+      }
+      P->graph = g;
+      P->gexec = ge;
+      P->graph_ok = true;
+    }
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    if (P->graph_ok) CK(cudaGraphLaunch(P->gexec, P->stream));
+    else enqueue_step(P);
+  }
+  CK(cudaGetLastError());
+  return SYMBA_OK;
+}
+
+int pool_create(symba_pool **out, int max_disks, long long max_particles, long long max_tiles,
+                long long pair_total, int precision, void *stream) {
+  if (!out || max_disks < 1 || max_particles < 1 || max_tiles < 1) return SYMBA_E_INVAL;
+  if (precision != SYMBA_PRECISION_FP64 && precision != SYMBA_PRECISION_MIXED) return SYMBA_E_INVAL;
+  symba_pool *P = new symba_pool();
+  *out = nullptr;
+  CK(cudaGetDevice(&P->device));
+  P->max_disks = max_disks;
+  P->precision = precision;
+  P->pcap = ((max_particles + SYM_TILE - 1) / SYM_TILE) * SYM_TILE + (long long)SYM_TILE * max_disks;
+  P->tcap = max_tiles;
+  P->paircap = pair_total;
+  if (stream) P->stream = (cudaStream_t)stream;
+  else {
+    if (cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking) != cudaSuccess) { delete P; return SYMBA_E_CUDA; }
+    P->own_stream = true;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, P->device) != cudaSuccess) { delete P; return SYMBA_E_CUDA; }
+  P->L.sms = prop.multiProcessorCount;
+  P->L.trap_blocks = P->L.sms * trap_blocks_per_sm(precision);
+  P->L.rec_blocks = P->L.sms * recursion_blocks_per_sm();
+  const long long n = P->pcap, pc = P->paircap, gs = n / 2 + 1;
+  Dev &D = P->D;
+  int st = SYMBA_OK;
+  auto A = [&](auto **ptr, size_t cnt) { if (st == SYMBA_OK) st = dalloc(P, ptr, cnt); };
+  A(&D.x, n); A(&D.y, n); A(&D.z, n); A(&D.vx, n); A(&D.vy, n); A(&D.vz, n);
+  A(&D.m, n); A(&D.gm, n); A(&D.rad, n); A(&D.rh, n);
+  A(&D.alive, n); A(&D.gid, n);
+  A(&D.xf, n); A(&D.yf, n); A(&D.zf, n); A(&D.vxf, n); A(&D.vyf, n); A(&D.vzf, n);
+  A(&D.lamf, n); A(&D.sigf, n); A(&D.xl, n); A(&D.yl, n); A(&D.zl, n); A(&D.gmf, n);
+  A(&D.blk_disk, n / SYM_TILE + 1);
+  A(&D.disks, max_disks); A(&D.stat, max_disks); A(&D.P, 3 * max_disks);
+  A(&D.sacc, (size_t)max_disks * 3 * (SA_NDIG + 1));
+  A(&D.tiles, P->tcap);
+  A(&D.part, (size_t)P->tcap * 2 * 3 * 32);
+  A(&D.work, 4);
+  A(&D.raw_i, pc); A(&D.raw_j, pc); A(&D.pi, pc); A(&D.pj, pc); A(&D.gop, pc);
+  A(&D.gpi, pc); A(&D.gpj, pc); A(&D.lev, pc); A(&D.tmpj, pc);
+  A(&D.perm, pc); A(&D.ptmp, pc); A(&D.pR0, pc); A(&D.pinvR0, pc);
+  A(&D.mperm, n); A(&D.mtmp, n);
+  A(&D.pf, 5 * pc); A(&D.adj, 2 * pc);
+  A(&D.cnt, n); A(&D.start, n); A(&D.cursor, n); A(&D.parent, n); A(&D.inpair, n);
+  A(&D.gidx, n); A(&D.mslot, n); A(&D.adj_off, n); A(&D.adj_cnt, n);
+  A(&D.acc, 3 * n);
+  A(&D.g_moff, gs); A(&D.g_mcnt, gs); A(&D.g_poff, gs); A(&D.g_pcnt, gs); A(&D.g_cur, gs);
+  A(&D.gmem, n); A(&D.rec_items, gs); A(&D.rec_total, 1);
+  A(&P->eacc, 4 * (SA_NDIG + 1)); A(&P->eout, 4);
+  if (st != SYMBA_OK) { symba_pool_free(P); return st; }
+  if (cudaMemsetAsync(D.blk_disk, 0xFF, sizeof(int) * (n / SYM_TILE + 1), P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.disks, 0, sizeof(DiskDesc) * max_disks, P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.stat, 0, sizeof(DiskStat) * max_disks, P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.work, 0, sizeof(int) * 4, P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.sacc, 0, sizeof(unsigned long long) * max_disks * 3 * (SA_NDIG + 1), P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.rec_total, 0, sizeof(int), P->stream) != cudaSuccess ||
+      cudaMemsetAsync(D.alive, 0, sizeof(int) * n, P->stream) != cudaSuccess) {
+    symba_pool_free(P);
+    return SYMBA_E_CUDA;
+  }
+  P->slots.assign(max_disks, Slot());
+  P->parts.init(n);
+  P->pairs.init(pc);
+  *out = P;
+  return SYMBA_OK;
+}
+
+int pool_admit(symba_pool *P, const symba_params *p, int n, int nm, const double *x, const double *v,
+               const double *m, const double *radius, const double *rhill, int *slot) {
+  if (!P || !p || !x || !v || !m || !radius || n < 1 || nm < 0 || nm > n) return SYMBA_E_INVAL;
+  if (p->dt == 0.0 || !(p->shell_ratio > 1.0) || p->M < 1 || p->l < 1 || p->max_depth < 1 ||
+      !(p->m0 > 0.0) || !(p->hill_scale >= 0.0))
+    return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  int d = -1;
+  for (int k = 0; k < P->max_disks; ++k) if (!P->slots[k].active) { d = k; break; }
+  if (d < 0) return SYMBA_E_NOMEM;
+  Slot s;
+  s.n = n; s.nm = nm; s.p = *p;
+  s.nb = (n + SYM_TILE - 1) / SYM_TILE;
+  s.nbm = (nm + SYM_TILE - 1) / SYM_TILE;
+  s.ntiles = (int)tiles_of(s.nb, s.nbm);
+  s.pair_cap = default_pair_cap(p, n);
+  if (P->tiles_used + s.ntiles > P->tcap) return SYMBA_E_NOMEM;
+  const long long po = P->parts.alloc((long long)s.nb * SYM_TILE);
+  if (po < 0) return SYMBA_E_NOMEM;
+  const long long pb = P->pairs.alloc(s.pair_cap);
+  if (pb < 0) { P->parts.release(po, (long long)s.nb * SYM_TILE); return SYMBA_E_NOMEM; }
+  s.off = (int)po;
+  s.pair_base = (int)pb;
+  s.active = true;
+  P->slots[d] = s;
+  P->tiles_used += s.ntiles;
+  // block -> system map
+  std::vector<int> bd(s.nb, d);
+  CK(cudaMemcpyAsync(P->D.blk_disk + s.off / SYM_TILE, bd.data(), sizeof(int) * s.nb, cudaMemcpyHostToDevice, P->stream));
+  int st = rebuild(P);
+  if (st != SYMBA_OK) return st;
+  launch_setup_disk(P->D, d, P->stream);
+  Staged sx, sv, sm, sr, sh;
+  if ((st = stage_in(sx, x, sizeof(double) * 3 * n, P->stream)) != SYMBA_OK) return st;
+  if ((st = stage_in(sv, v, sizeof(double) * 3 * n, P->stream)) != SYMBA_OK) return st;
+  if ((st = stage_in(sm, m, sizeof(double) * n, P->stream)) != SYMBA_OK) return st;
+  if ((st = stage_in(sr, radius, sizeof(double) * n, P->stream)) != SYMBA_OK) return st;
+  if ((st = stage_in(sh, rhill, sizeof(double) * n, P->stream)) != SYMBA_OK) return st;
+  launch_init_state(P->D, d, n, (const double *)sx.dev, (const double *)sv.dev, (const double *)sm.dev,
+                    (const double *)sr.dev, (const double *)sh.dev, rhill == nullptr ? 1 : 0, P->stream);
+  launch_momentum(P->D, P->ndisks, P->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(P->stream));  // staging buffers are freed on return
+  if (slot) *slot = d;
+  return SYMBA_OK;
+}
+
+int read_stat(symba_pool *P, int d, DiskStat *out) {
+  CK(cudaStreamSynchronize(P->stream));
+  CK(cudaMemcpy(out, P->D.stat + d, sizeof(DiskStat), cudaMemcpyDeviceToHost));
+  return SYMBA_OK;
+}
+
+int slot_status(symba_pool *P, int d) {
+  DiskStat st;
+  int r = read_stat(P, d, &st);
+  if (r != SYMBA_OK) return r;
+  if (st.status != 0) return st.status;
+  Slot &s = P->slots[d];
+  if ((long long)st.merges > s.merges_reported) {
+    s.merges_reported = (long long)st.merges;
+    return SYMBA_COLLISION;
+  }
+  return SYMBA_OK;
+}
+
+bool valid_slot(symba_pool *P, int d) { return P && d >= 0 && d < P->max_disks && P->slots[d].active; }
+
+int get_state(symba_pool *P, int d, double *x, double *v, double *m, double *rad, int *alive) {
+  if (!valid_slot(P, d)) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  const int n = P->slots[d].n;
+  double *dx = nullptr, *dv = nullptr, *dm = nullptr, *dr = nullptr;
+  int *da = nullptr;
+  const bool hx = x && !is_device_ptr(x), hv = v && !is_device_ptr(v), hm = m && !is_device_ptr(m),
+             hr = rad && !is_device_ptr(rad), ha = alive && !is_device_ptr(alive);
+  int st = SYMBA_OK;
+  auto tmp = [&](bool need, void **pp, size_t bytes) {
+    if (need && st == SYMBA_OK && cudaMalloc(pp, bytes) != cudaSuccess) st = SYMBA_E_NOMEM;
+  };
+  tmp(hx, (void **)&dx, sizeof(double) * 3 * n);
+  tmp(hv, (void **)&dv, sizeof(double) * 3 * n);
+  tmp(hm, (void **)&dm, sizeof(double) * n);
+  tmp(hr, (void **)&dr, sizeof(double) * n);
+  tmp(ha, (void **)&da, sizeof(int) * n);
+  if (st == SYMBA_OK) {
+    launch_gather_state(P->D, d, n, hx ? dx : x, hv ? dv : v, hm ? dm : m, hr ? dr : rad, ha ? da : alive, P->stream);
+    if (hx) cudaMemcpyAsync(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, P->stream);
+    if (hv) cudaMemcpyAsync(v, dv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, P->stream);
+    if (hm) cudaMemcpyAsync(m, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream);
+    if (hr) cudaMemcpyAsync(rad, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream);
+    if (ha) cudaMemcpyAsync(alive, da, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream);
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) st = SYMBA_E_CUDA;
+  }
+  cudaFree(dx); cudaFree(dv); cudaFree(dm); cudaFree(dr); cudaFree(da);
+  if (st != SYMBA_OK) return st;
+  return slot_status(P, d);
+}
+
+int set_state(symba_pool *P, int d, const double *x, const double *v) {
+  if (!valid_slot(P, d) || !x || !v) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  const int n = P->slots[d].n;
+  Staged sx, sv;
+  int st;
+  if ((st = stage_in(sx, x, sizeof(double) * 3 * n, P->stream)) != SYMBA_OK) return st;
+  if ((st = stage_in(sv, v, sizeof(double) * 3 * n, P->stream)) != SYMBA_OK) return st;
+  launch_scatter_state(P->D, d, n, (const double *)sx.dev, (const double *)sv.dev, P->stream);
+  launch_momentum(P->D, P->ndisks, P->stream);
+  CK(cudaMemsetAsync(&P->D.stat[d].status, 0, sizeof(int), P->stream));
+  CK(cudaGetLastError());
+  if (sx.own || sv.own) CK(cudaStreamSynchronize(P->stream));
+  return SYMBA_OK;
+}
+
+int energy(symba_pool *P, int d, double *E, double *L) {
+  if (!valid_slot(P, d) || !E) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  CK(cudaMemsetAsync(P->eacc, 0, sizeof(unsigned long long) * 4 * (SA_NDIG + 1), P->stream));
+  launch_energy(P->D, d, P->L, P->eacc, P->stream);
+  launch_energy_round(P->eacc, P->eout, P->stream);
+  double out[4];
+  CK(cudaMemcpyAsync(out, P->eout, sizeof(out), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  *E = out[0];
+  if (L) { L[0] = out[1]; L[1] = out[2]; L[2] = out[3]; }
+  return slot_status(P, d);
+}
+
+__global__ void k_pairs_out(Dev D, int d, int cap, int *pairs, int *gop) {
+  const DiskDesc dd = D.disks[d];
+  int np = D.stat[d].npairs;
+  if (np > dd.pair_cap) np = dd.pair_cap;
+  const int lim = np < cap ? np : cap;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < lim; q += gridDim.x * blockDim.x) {
+    if (pairs) {
+      pairs[2 * q] = D.pi[dd.pair_base + q] - dd.off;
+      pairs[2 * q + 1] = D.pj[dd.pair_base + q] - dd.off;
+    }
+    if (gop) gop[q] = D.gop[dd.pair_base + q];
+  }
+}
+
+int enc_groups(symba_pool *P, int d, int *pairs, int *gop, int cap, int *npairs, int *ngroups) {
+  if (!valid_slot(P, d) || cap < 0) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  DiskStat st;
+  int r = read_stat(P, d, &st);
+  if (r != SYMBA_OK) return r;
+  if (npairs) *npairs = st.npairs;
+  if (ngroups) *ngroups = st.ngroups;
+  const int lim = std::min(std::min(st.npairs, P->slots[d].pair_cap), cap);
+  if (lim > 0 && (pairs || gop)) {
+    const bool hp = pairs && !is_device_ptr(pairs), hg = gop && !is_device_ptr(gop);
+    int *dp = nullptr, *dg = nullptr;
+    if (hp && cudaMalloc(&dp, sizeof(int) * 2 * lim) != cudaSuccess) return SYMBA_E_NOMEM;
+    if (hg && cudaMalloc(&dg, sizeof(int) * lim) != cudaSuccess) { cudaFree(dp); return SYMBA_E_NOMEM; }
+    k_pairs_out<<<64, 256, 0, P->stream>>>(P->D, d, lim, hp ? dp : pairs, hg ? dg : gop);
+    if (hp) cudaMemcpyAsync(pairs, dp, sizeof(int) * 2 * lim, cudaMemcpyDeviceToHost, P->stream);
+    if (hg) cudaMemcpyAsync(gop, dg, sizeof(int) * lim, cudaMemcpyDeviceToHost, P->stream);
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    cudaFree(dp);
+    cudaFree(dg);
+    if (e != cudaSuccess) return SYMBA_E_CUDA;
+  }
+  return slot_status(P, d);
+}
+
+int get_stats(symba_pool *P, int d, symba_stats *out) {
+  if (!valid_slot(P, d) || !out) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  DiskStat st;
+  int r = read_stat(P, d, &st);
+  if (r != SYMBA_OK) return r;
+  out->n_pairs = st.npairs;
+  out->n_groups = st.ngroups;
+  out->max_depth = st.max_depth;
+  out->status = st.status;
+  out->merges = (long long)st.merges;
+  out->substeps = (long long)st.substeps;
+  out->steps = 0;
+  return SYMBA_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+void symba_default_params(symba_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->dt = 0.5;
+  p->shell_ratio = 2.08;
+  p->hill_scale = 6.5;
+  p->G = 4.0 * M_PI * M_PI;
+  p->m0 = 1.0;
+  p->M = 4;
+  p->l = 3;
+  p->max_depth = 20;
+  p->precision = SYMBA_PRECISION_FP64;
+  p->pair_capacity = 0;
+  p->max_substeps = 0;
+}
+
+const char *symba_status_string(int s) {
+  switch (s) {
+    case SYMBA_OK: return "ok";
+    case SYMBA_COLLISION: return "bodies merged";
+    case SYMBA_E_INVAL: return "invalid argument";
+    case SYMBA_E_NOMEM: return "out of device memory or pool capacity";
+    case SYMBA_E_CUDA: return "CUDA runtime error";
+    case SYMBA_E_KEPLER: return "Kepler's equation did not converge";
+    case SYMBA_E_DEPTH: return "recursion deeper than max_depth or sub-step budget exhausted";
+    case SYMBA_E_CAPACITY: return "encounter pair list overflow";
+    case SYMBA_E_NONFINITE: return "non-finite state";
+    default: return "unknown status";
+  }
+}
+
+long long symba_pool_footprint(int n, int n_massive, const symba_params *p) {
+  if (n < 1 || n_massive < 0 || n_massive > n) return -1;
+  const long long nb = (n + SYM_TILE - 1) / SYM_TILE, nbm = (n_massive + SYM_TILE - 1) / SYM_TILE;
+  const long long np = nb * SYM_TILE;
+  const long long per_particle = 10 * 8 + 2 * 4 + 11 * 4 + 12 * 4 + 3 * 8 + 6 * 4 / 2 + 4;
+  const long long pairs = default_pair_cap(p, n);
+  const long long per_pair = 11 * 4 + 7 * 8 + 2 * 4;
+  return np * per_particle + pairs * per_pair + tiles_of((int)nb, (int)nbm) * (16 + 2 * 3 * 32 * 8);
+}
+
+int symba_pool_create(symba_pool **out, int max_systems, long long max_particles, long long max_tiles,
+                      int precision, void *cuda_stream) {
+  const long long pair_total = std::max(4LL * max_particles, 4096LL) + 4096LL * max_systems;
+  return pool_create(out, max_systems, max_particles, max_tiles, pair_total, precision, cuda_stream);
+}
+
+int symba_pool_admit(symba_pool *pool, const symba_params *p, int n, int n_massive, const double *x,
+                     const double *v, const double *m, const double *radius, const double *rhill,
+                     int *slot) {
+  if (!pool || !p) return SYMBA_E_INVAL;
+  if (p->precision != pool->precision) return SYMBA_E_INVAL;
+  return pool_admit(pool, p, n, n_massive, x, v, m, radius, rhill, slot);
+}
+
+int symba_pool_step(symba_pool *pool, int nsteps) {
+  if (!pool) return SYMBA_E_INVAL;
+  return pool_step(pool, nsteps);
+}
+
+int symba_pool_sync(symba_pool *pool) {
+  if (!pool) return SYMBA_E_INVAL;
+  if (cudaStreamSynchronize(pool->stream) != cudaSuccess) return SYMBA_E_CUDA;
+  int worst = SYMBA_OK;
+  for (int d = 0; d < pool->max_disks; ++d) {
+    if (!pool->slots[d].active) continue;
+    const int s = slot_status(pool, d);
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (s > 0 && worst == SYMBA_OK) worst = s;
+  }
+  return worst;
+}
+
+int symba_pool_get_state(symba_pool *pool, int slot, double *x, double *v, double *m, double *radius,
+                         int *alive) {
+  return get_state(pool, slot, x, v, m, radius, alive);
+}
+
+int symba_pool_energy(symba_pool *pool, int slot, double *E, double L[3]) { return energy(pool, slot, E, L); }
+
+int symba_pool_get_stats(symba_pool *pool, int slot, symba_stats *s) { return get_stats(pool, slot, s); }
+
+int symba_pool_evict(symba_pool *pool, int slot) {
+  if (!valid_slot(pool, slot)) return SYMBA_E_INVAL;
+  if (cudaStreamSynchronize(pool->stream) != cudaSuccess) return SYMBA_E_CUDA;
+  Slot &s = pool->slots[slot];
+  std::vector<int> bd(s.nb, -1);
+  if (cudaMemcpy(pool->D.blk_disk + s.off / SYM_TILE, bd.data(), sizeof(int) * s.nb, cudaMemcpyHostToDevice) != cudaSuccess)
+    return SYMBA_E_CUDA;
+  pool->parts.release(s.off, (long long)s.nb * SYM_TILE);
+  pool->pairs.release(s.pair_base, s.pair_cap);
+  pool->tiles_used -= s.ntiles;
+  s = Slot();
+  return rebuild(pool);
+}
+
+void symba_pool_free(symba_pool *pool) {
+  if (!pool) return;
+  if (pool->stream) cudaStreamSynchronize(pool->stream);
+  invalidate_graph(pool);
+  for (void *p : pool->allocs) cudaFree(p);
+  if (pool->own_stream && pool->stream) cudaStreamDestroy(pool->stream);
+  delete pool;
+}
+
+int symba_init(symba_ctx **out, const symba_params *p, int n, int n_massive, const double *x,
+               const double *v, const double *m, const double *radius, const double *rhill,
+               void *cuda_stream) {
+  if (!out || !p || n < 1 || n_massive < 0 || n_massive > n) return SYMBA_E_INVAL;
+  *out = nullptr;
+  symba_pool *P = nullptr;
+  const long long nb = (n + SYM_TILE - 1) / SYM_TILE, nbm = (n_massive + SYM_TILE - 1) / SYM_TILE;
+  const long long tiles = std::max(1LL, tiles_of((int)nb, (int)nbm));
+  int st = pool_create(&P, 1, n, tiles, default_pair_cap(p, n), p->precision, cuda_stream);
+  if (st != SYMBA_OK) return st;
+  int slot = -1;
+  st = pool_admit(P, p, n, n_massive, x, v, m, radius, rhill, &slot);
+  if (st != SYMBA_OK) { symba_pool_free(P); return st; }
+  symba_ctx *c = new symba_ctx{P, slot};
+  *out = c;
+  return SYMBA_OK;
+}
+
+int symba_step(symba_ctx *c, int nsteps) {
+  if (!c) return SYMBA_E_INVAL;
+  return pool_step(c->pool, nsteps);
+}
+
+int symba_sync(symba_ctx *c) {
+  if (!c) return SYMBA_E_INVAL;
+  return slot_status(c->pool, c->slot);
+}
+
+int symba_energy(symba_ctx *c, double *E, double L[3]) {
+  if (!c) return SYMBA_E_INVAL;
+  return energy(c->pool, c->slot, E, L);
+}
+
+int symba_enc_groups(symba_ctx *c, int *pairs, int *group_of_pair, int cap, int *n_pairs, int *n_groups) {
+  if (!c) return SYMBA_E_INVAL;
+  return enc_groups(c->pool, c->slot, pairs, group_of_pair, cap, n_pairs, n_groups);
+}
+
+int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radius, int *alive) {
+  if (!c) return SYMBA_E_INVAL;
+  return get_state(c->pool, c->slot, x, v, m, radius, alive);
+}
+
+int symba_set_state(symba_ctx *c, const double *x, const double *v) {
+  if (!c) return SYMBA_E_INVAL;
+  return set_state(c->pool, c->slot, x, v);
+}
+
+int symba_get_stats(symba_ctx *c, symba_stats *s) {
+  if (!c) return SYMBA_E_INVAL;
+  return get_stats(c->pool, c->slot, s);
+}
+
+int symba_profile_step(symba_ctx *c, int nsteps, double *phase_ms) {
+  if (!c) return SYMBA_E_INVAL;
+  const int rc = pool_profile(c->pool, nsteps, phase_ms);
+  if (rc != SYMBA_OK) return rc;
+  return slot_status(c->pool, c->slot);
+}
+
+void symba_free(symba_ctx *c) {
+  if (!c) return;
+  symba_pool_free(c->pool);
+  delete c;
+}
+
+}  // extern "C"

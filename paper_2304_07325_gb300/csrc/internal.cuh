@@ -1,0 +1,492 @@
+// Internal data layout and device helpers of the SyMBA GB300 path.
+//
+// Layout in HBM (all systems of a pool share the arrays; system d owns particles
+// [off_d, off_d + n_d), off_d a multiple of 32):
+//   x, y, z, vx, vy, vz, m, gm (= G m), rad, rh   : FP64 SoA, heliocentric x, barycentric v
+//   alive, gid                                     : int per particle (gid = encounter group or -1)
+//   xf, yf, zf, vxf, vyf, vzf, lamf, sigf          : FP32 copies for the encounter prefilter
+//   tiles                                          : int4 {system, I-block, J-block, 0} per 32x32 tile
+//   part                                           : FP64 [tile][2 sides][3][32] pair-kick partials
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/symba.h"
+
+#define SYM_TILE 32
+#define SYM_MAX_LEVELS 32
+#define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
+
+struct DiskDesc {
+  int off, n, nm, nb, nbm;      // first particle, counts, 32-blocks (all, massive rows)
+  int tile_base, ntiles;        // this system's tiles in the global tile list
+  int pair_base, pair_cap;      // this system's slice of the pair buffers
+  int group_base;               // this system's slice of the group slots (= off / 2)
+  int active, M, l, max_depth, max_substeps, pad0;
+  double dt, shell_ratio, hill_scale, G, m0;
+  double ck[SYM_MAX_LEVELS + 2];    // c_k = c_{k-1} / shell_ratio, c_0 = 1 (R_k = R_0 c_k)
+  double ck2[SYM_MAX_LEVELS + 2];   // c_k^2
+  double invdc[SYM_MAX_LEVELS + 2]; // 1 / (c_k - c_{k+1})
+};
+
+struct DiskStat {               // mutable per-system counters (device)
+  int npairs, ngroups, status, max_depth;
+  unsigned long long merges, substeps, merges_reported;
+};
+
+struct Dev {
+  // particle SoA
+  double *x, *y, *z, *vx, *vy, *vz, *m, *gm, *rad, *rh;
+  int *alive, *gid;
+  float *xf, *yf, *zf, *vxf, *vyf, *vzf, *lamf, *sigf;
+  float *xl, *yl, *zl;          // low parts of positions (mixed precision: x = xf + xl)
+  float *gmf;                   // G m in FP32 (mixed precision)
+  int *blk_disk;                // system of each 32-block
+  // systems
+  DiskDesc *disks;
+  DiskStat *stat;
+  double *P;                    // [max_disks][3] total barycentric momentum (for the sun drift)
+  unsigned long long *sacc;     // [max_disks][3][SA_NDIG + 1] exact accumulators
+  // trapezoid
+  int4 *tiles;
+  double *part;                 // [tile][2][3][32]
+  int *work;                    // [4] dynamic work counters (kick 1, kick 2, recursion, spare)
+  int ntiles_total;
+  int seg_len;                  // tiles per work item
+  int ndisks;                   // slots in use (upper bound of active slots)
+  // encounter pairs (pair-indexed, per-system slices)
+  int *raw_i, *raw_j;           // appended by the fused check, unordered
+  int *pi, *pj, *gop;           // sorted (i, j) and group of each pair (local group index)
+  int *gpi, *gpj;               // pairs grouped by group, sorted within a group (global indices)
+  int *lev;                     // recursion level marks per grouped pair
+  int *perm, *ptmp;             // nested active-pair lists of the recursion (per grouped pair)
+  double *pR0, *pinvR0;         // level-0 critical radius of each grouped pair and its inverse
+  int *mperm, *mtmp;            // nested active-member lists (per member slot)
+  double *pf;                   // [pair][5] per-pair force scratch (d, fi, fj)
+  int *adj;                     // [2 * pair] adjacency: (grouped pair index << 1) | side
+  // particle-indexed scratch for grouping
+  int *cnt, *start, *cursor, *parent, *inpair, *gidx, *tmpj, *mslot, *adj_off, *adj_cnt;
+  double *acc;                  // [particle][3] recursion accelerations
+  // groups (group slots, per-system slices)
+  int *g_moff, *g_mcnt, *g_poff, *g_pcnt, *g_cur;
+  int *gmem;                    // members grouped by group (global particle indices)
+  int *rec_items;               // recursion work list (global group slot)
+  int *rec_total;               // number of items
+};
+
+// --------------------------------------------------------------------------------------------
+// small helpers
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(DiskStat *st, int code) {
+  atomicCAS(&st->status, 0, code);
+}
+
+__device__ __forceinline__ int find_disk(const int *blk_disk, int p) { return blk_disk[p >> 5]; }
+
+// r^-3 for the pair kick: seed 1/sqrt(r2) from the top 23 mantissa bits of r2 with one MUFU
+// rsqrt (exponent re-biased with integer operations, so no FP64 conversion is issued), then the
+// third-order correction r^-3 = y0^3 (1 - e)^{-3/2} ~ y0^3 (1 + 3/2 e + 15/8 e^2),
+// e = 1 - r2 y0^2 (|e| < 2^-19, truncation < 2^-57): 6 FP64 instructions.  Values of r2 outside
+// the normal FP32 range take the library path.
+__device__ __forceinline__ double rinv3(double r2) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int fe = ((hi >> 20) & 0x7FF) - 896;
+  if ((unsigned)(fe - 1) <= 253u && hi > 0) {
+    const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+    const float r2f = __uint_as_float(((unsigned)fe << 23) | m23);
+    float y0f;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2f));
+    const unsigned yb = __float_as_uint(y0f);
+    const int ye = (int)((yb >> 23) & 0xFF) + 896;
+    const double y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
+    const double t = y0 * y0;          // exact: y0 has 24 significant bits
+    const double y03 = t * y0;
+    const double e = fma(-r2, t, 1.0);
+    const double p = fma(e, 1.875, 1.5);
+    const double ep = e * p;
+    return fma(y03, ep, y03);
+  }
+  const double y = rsqrt(r2);
+  return y * y * y;
+}
+
+// 1/sqrt(r2) to full FP64 accuracy: the same integer-built FP32 seed, then the third-order
+// correction y = y0 (1 + e/2 + 3e^2/8), e = 1 - r2 y0^2 (5 FP64 instructions).
+__device__ __forceinline__ double rsqrt_fp64(double r2) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int fe = ((hi >> 20) & 0x7FF) - 896;
+  if ((unsigned)(fe - 1) <= 253u && hi > 0) {
+    const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+    const float r2f = __uint_as_float(((unsigned)fe << 23) | m23);
+    float y0f;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2f));
+    const unsigned yb = __float_as_uint(y0f);
+    const int ye = (int)((yb >> 23) & 0xFF) + 896;
+    const double y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
+    const double e = fma(-r2, y0 * y0, 1.0);
+    return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+  }
+  return rsqrt(r2);
+}
+
+// Select without arithmetic: v if keep, else 0.0 (integer select on the bit pattern).
+__device__ __forceinline__ double keep_or_zero(double v, bool keep) {
+  long long b = __double_as_longlong(v);
+  return __longlong_as_double(keep ? b : 0ll);
+}
+
+// --------------------------------------------------------------------------------------------
+// Close-encounter predicate over an interval h at critical radius R: minimum distance of the
+// straight-line relative motion below R (strict).  Every operation is one IEEE FP64 operation
+// in a fixed order without contraction, so every caller on any device decides identically on
+// identical inputs.  d = x_b - x_a, dv = v_b - v_a (either order gives the same bits).
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool encounter_exact(double dx, double dy, double dz, double dvx,
+                                                double dvy, double dvz, double R, double h) {
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
+  const double vr = __dadd_rn(__dadd_rn(__dmul_rn(dx, dvx), __dmul_rn(dy, dvy)), __dmul_rn(dz, dvz));
+  const double R2 = __dmul_rn(R, R);
+  if (r2 < R2) return true;
+  if (vr >= 0.0) return false;
+  const double t = __ddiv_rn(-vr, v2);
+  if (t < h) return __dsub_rn(r2, __ddiv_rn(__dmul_rn(vr, vr), v2)) < R2;
+  return __dadd_rn(r2, __dmul_rn(h, __dadd_rn(__dmul_rn(2.0, vr), __dmul_rn(h, v2)))) < R2;
+}
+
+// Partition function of order l: the degree-(2l+1) polynomial rising from 0 to 1 on [0, 1]
+// with its first l derivatives zero at both ends, f_l(x) = x^{l+1} sum_k C(l+k,k) C(2l+1,l-k)
+// (-x)^k, clamped outside [0, 1] (Sec. 3 uses l = 3).
+__device__ __forceinline__ double binom_d(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+  return r;
+}
+
+__device__ __forceinline__ double partition_fn(double x, int l) {
+  if (x <= 0.0) return 0.0;
+  if (x >= 1.0) return 1.0;
+  if (l == 3) {
+    // x^4 (35 - 84 x + 70 x^2 - 20 x^3)
+    const double x2 = x * x;
+    return x2 * x2 * fma(x, fma(x, fma(x, -20.0, 70.0), -84.0), 35.0);
+  }
+  double s = 0.0, xk = 1.0;
+  for (int k = 0; k <= l; ++k) {
+    s += binom_d(l + k, k) * binom_d(2 * l + 1, l - k) * xk;
+    xk *= -x;
+  }
+  double xp = 1.0;
+  for (int k = 0; k <= l; ++k) xp *= x;
+  return xp * s;
+}
+
+// g_k(r): share of a pair force kept at levels <= k (1 outside R_k, 0 inside R_{k+1}).
+__device__ __forceinline__ double g_level(const DiskDesc &dd, double R0, int k, double r) {
+  const double Rk = R0 * dd.ck[k], Rk1 = R0 * dd.ck[k + 1];
+  return partition_fn((r - Rk1) / (Rk - Rk1), dd.l);
+}
+
+// Level-k weight of a pair force: w_0 = g_0, w_k = g_k - g_{k-1}.
+__device__ __forceinline__ double level_weight(const DiskDesc &dd, double R0, int k, double r) {
+  if (k == 0) return g_level(dd, R0, 0, r);
+  return g_level(dd, R0, k, r) - g_level(dd, R0, k - 1, r);
+}
+
+// --------------------------------------------------------------------------------------------
+// Exact accumulation of doubles: 68 signed 32-bit-digit slots in int64 (carry-save), digit k
+// weighing 2^(32k - 1088), plus one slot counting non-finite inputs.  Integer addition is
+// associative, so the total is independent of the order of the atomics; sa_round returns it
+// correctly rounded to nearest-even.
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ void sa_add(unsigned long long *dig, double x) {
+  if (x == 0.0) return;
+  const long long bits = __double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7FF);
+  unsigned long long mant = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  if (ex == 0x7FF) { atomicAdd(&dig[SA_NDIG], 1ull); return; }
+  if (ex == 0) ex = 1; else mant |= 1ull << 52;
+  const int p = ex + 13;  // weight of the mantissa's lowest bit, in units of 2^-1088
+  const int k = p >> 5, sh = p & 31;
+  const unsigned long long lo = mant << sh;
+  const unsigned long long hi = sh ? (mant >> (64 - sh)) : 0ull;
+  long long c0 = (long long)(lo & 0xFFFFFFFFull), c1 = (long long)(lo >> 32), c2 = (long long)hi;
+  if (bits < 0) { c0 = -c0; c1 = -c1; c2 = -c2; }
+  if (c0) atomicAdd(&dig[k], (unsigned long long)c0);
+  if (c1) atomicAdd(&dig[k + 1], (unsigned long long)c1);
+  if (c2) atomicAdd(&dig[k + 2], (unsigned long long)c2);
+}
+
+__device__ inline double sa_round(const unsigned long long *in) {
+  if (in[SA_NDIG] != 0ull) return __longlong_as_double(0x7FF8000000000000ll);
+  long long d[SA_NDIG];
+  for (int k = 0; k < SA_NDIG; ++k) d[k] = (long long)in[k];
+  for (int k = 0; k < SA_NDIG - 1; ++k) {
+    const long long c = d[k] >> 32;
+    d[k] -= c * 4294967296ll;
+    d[k + 1] += c;
+  }
+  const bool neg = d[SA_NDIG - 1] < 0;
+  if (neg) {
+    for (int k = 0; k < SA_NDIG; ++k) d[k] = -d[k];
+    for (int k = 0; k < SA_NDIG - 1; ++k) {
+      const long long c = d[k] >> 32;
+      d[k] -= c * 4294967296ll;
+      d[k + 1] += c;
+    }
+  }
+  int t = SA_NDIG - 1;
+  while (t >= 0 && d[t] == 0) --t;
+  if (t < 0) return 0.0;
+  const unsigned long long dt = (unsigned long long)d[t];
+  const unsigned long long d1 = t >= 1 ? (unsigned long long)d[t - 1] : 0ull;
+  const unsigned long long d2 = t >= 2 ? (unsigned long long)d[t - 2] : 0ull;
+  bool sticky = false;
+  for (int k = 0; k < t - 2; ++k) sticky |= (d[k] != 0);
+  const int lz = __clz((unsigned)dt);
+  const unsigned long long H = (dt << 32) | d1;
+  unsigned long long T;
+  if (lz == 0) {
+    T = H;
+    sticky |= (d2 != 0ull);
+  } else {
+    T = (H << lz) | (d2 >> (32 - lz));
+    sticky |= ((d2 << lz) & 0xFFFFFFFFull) != 0ull;
+  }
+  int E = t * 32 + 31 - lz - 1088;  // exponent of the leading bit
+  double r;
+  if (E < -1022) {
+    // below the normal range the exact sum (a multiple of 2^-1074) is representable
+    r = 0.0;
+    for (int k = t; k >= 0; --k) r += ldexp((double)d[k], 32 * k - 1088);
+  } else {
+    unsigned long long mant = T >> 11;
+    const bool rbit = (T >> 10) & 1ull;
+    sticky |= (T & 0x3FFull) != 0ull;
+    if (rbit && (sticky || (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) { mant >>= 1; ++E; }
+    }
+    if (E > 1023) r = __longlong_as_double(0x7FF0000000000000ll);
+    else r = ldexp((double)mant, E - 52);
+  }
+  return neg ? -r : r;
+}
+
+// --------------------------------------------------------------------------------------------
+// Kepler drift (Danby 1988, f and g functions): advance (x, v) by dt on the orbit of parameter
+// mu.  Elliptic orbits solve for the eccentric-anomaly difference X of
+//   X - ec sin X + es (1 - cos X) = n dt,  ec = 1 - r0/a, es = u / (n a^2)
+// with Danby's quartically convergent iteration from X = n dt, falling back to a bracketed
+// Newton-bisection; other orbits use universal variables with Stumpff functions.
+// Returns SYMBA_OK or SYMBA_E_KEPLER / SYMBA_E_NONFINITE.
+// --------------------------------------------------------------------------------------------
+__device__ inline void stumpff4(double z, double c[4]) {
+  if (fabs(z) < 0.1) {
+    for (int k = 0; k < 4; ++k) {
+      double term = 1.0, s = 0.0;
+      for (int i = 2; i <= k; ++i) term /= (double)i;
+      for (int j = 0; j < 24; ++j) {
+        s += term;
+        term *= -z / ((double)(2 * j + k + 1) * (double)(2 * j + k + 2));
+      }
+      c[k] = s;
+    }
+    return;
+  }
+  if (z > 0.0) {
+    const double sz = sqrt(z);
+    double sn, cs;
+    sincos(sz, &sn, &cs);
+    c[0] = cs;
+    c[1] = sn / sz;
+  } else {
+    const double sz = sqrt(-z);
+    c[0] = cosh(sz);
+    c[1] = sinh(sz) / sz;
+  }
+  c[2] = (1.0 - c[0]) / z;
+  c[3] = (1.0 - c[1]) / z;
+}
+
+__device__ inline int kepler_drift(double mu, double dt, double &x, double &y, double &z,
+                                   double &vx, double &vy, double &vz) {
+  const double r0 = sqrt(fma(z, z, fma(y, y, x * x)));
+  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+  const double u = fma(z, vz, fma(y, vy, x * vx));
+  const double alpha = 2.0 * mu / r0 - v2;
+  if (!(r0 > 0.0) || !isfinite(alpha) || !isfinite(u)) return SYMBA_E_NONFINITE;
+  double f, g, fdot, gdot;
+  if (alpha > 0.0) {
+    const double a = mu / alpha;
+    const double nn = sqrt(mu / (a * a * a));
+    const double ec = 1.0 - r0 / a;
+    const double es = u / (nn * a * a);
+    const double ndt = nn * dt;
+    double X = ndt, sx = 0.0, cx = 1.0;
+    bool ok = false;
+    for (int it = 0; it < 12; ++it) {
+      sincos(X, &sx, &cx);
+      const double omc = (cx > 0.0) ? sx * sx / (1.0 + cx) : 1.0 - cx;
+      const double F = X - ec * sx + es * omc - ndt;
+      const double Fp = 1.0 - ec * cx + es * sx;
+      const double Fpp = ec * sx + es * cx;
+      const double Fppp = ec * cx - es * sx;
+      const double d1 = -F / Fp;
+      const double d2 = -F / (Fp + 0.5 * d1 * Fpp);
+      const double d3 = -F / (Fp + 0.5 * d2 * Fpp + d2 * d2 * Fppp * (1.0 / 6.0));
+      X += d3;
+      if (fabs(d3) <= 1e-15 * fmax(1.0, fabs(X))) { ok = true; break; }
+    }
+    if (!ok) {
+      double lo = ndt - 2.5, hi = ndt + 2.5;
+      X = ndt;
+      for (int it = 0; it < 200; ++it) {
+        sincos(X, &sx, &cx);
+        const double omc = (cx > 0.0) ? sx * sx / (1.0 + cx) : 1.0 - cx;
+        const double F = X - ec * sx + es * omc - ndt;
+        const double Fp = 1.0 - ec * cx + es * sx;
+        if (F > 0.0) hi = X; else lo = X;
+        const double dX = -F / Fp;
+        double Xn = X + dX;
+        if (fabs(dX) <= 1e-15 * fmax(1.0, fabs(X))) { X = Xn; ok = true; break; }
+        if (!(Xn > lo && Xn < hi)) Xn = 0.5 * (lo + hi);
+        X = Xn;
+      }
+      if (!ok) return SYMBA_E_KEPLER;
+    }
+    sincos(X, &sx, &cx);
+    const double omc = (cx > 0.0) ? sx * sx / (1.0 + cx) : 1.0 - cx;
+    const double r = a * (1.0 - ec * cx + es * sx);
+    f = 1.0 - (a / r0) * omc;
+    g = dt - (X - sx) / nn;
+    fdot = -(a * a * nn * sx) / (r * r0);
+    gdot = 1.0 - (a / r) * omc;
+  } else {
+    const double sgn = dt >= 0.0 ? 1.0 : -1.0;
+    double c[4];
+    double lo = 0.0, hi = fabs(dt) / r0;
+    if (hi == 0.0) return SYMBA_OK;
+    bool found = false;
+    for (int it = 0; it < 200; ++it) {
+      const double s = sgn * hi;
+      stumpff4(alpha * s * s, c);
+      const double F = r0 * s * c[1] + u * s * s * c[2] + mu * s * s * s * c[3] - dt;
+      if (sgn * F >= 0.0) { found = true; break; }
+      lo = hi;
+      hi *= 2.0;
+    }
+    if (!found) return SYMBA_E_KEPLER;
+    double sa = 0.5 * (lo + hi);
+    bool ok = false;
+    for (int it = 0; it < 400; ++it) {
+      const double s = sgn * sa;
+      stumpff4(alpha * s * s, c);
+      const double G1 = s * c[1], G2 = s * s * c[2], G3 = s * s * s * c[3];
+      const double F = r0 * G1 + u * G2 + mu * G3 - dt;
+      const double Fp = r0 * c[0] + u * G1 + mu * G2;
+      if (sgn * F > 0.0) hi = sa; else lo = sa;
+      const double ds = -F / Fp;
+      double sn = sa + sgn * ds;
+      if (fabs(ds) <= 1e-15 * fmax(1e-300, fabs(sa))) { sa = sn; ok = true; break; }
+      if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+      sa = sn;
+    }
+    if (!ok) return SYMBA_E_KEPLER;
+    const double s = sgn * sa;
+    stumpff4(alpha * s * s, c);
+    const double G1 = s * c[1], G2 = s * s * c[2], G3 = s * s * s * c[3];
+    const double r = r0 * c[0] + u * G1 + mu * G2;
+    f = 1.0 - mu * G2 / r0;
+    g = dt - mu * G3;
+    fdot = -mu * G1 / (r * r0);
+    gdot = 1.0 - mu * G2 / r;
+  }
+  const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
+  x = f * x0 + g * vx0;
+  y = f * y0 + g * vy0;
+  z = f * z0 + g * vz0;
+  vx = fdot * x0 + gdot * vx0;
+  vy = fdot * y0 + gdot * vy0;
+  vz = fdot * z0 + gdot * vz0;
+  return SYMBA_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// Short-interval Kepler drift by the Lagrange f and g series (used on the deep recursion levels,
+// where the sub-step h is a tiny fraction of the orbit).  With u = mu/r^3, p = (x.v)/r^2,
+// q = v^2/r^2 - u, the derivatives of f and g obey f^(n+1) = (dA_n/dt - u B_n) f + (A_n + dB_n/dt) f'
+// with du/dt = -3up, dp/dt = q - 2p^2, dq/dt = -p(u + 2q), which gives, through t^6,
+//   f = 1 - u t^2/2 + u p t^3/2 + (3uq - 15up^2 + u^2) t^4/24 + (7up^3 - 3upq - u^2 p) t^5/8
+//       + (-945up^4 + 630up^2 q - 45uq^2 + 210u^2p^2 - 24u^2 q - u^3) t^6/720
+//   g = t - u t^3/6 + u p t^4/4 + (9uq - 45up^2 + u^2) t^5/120 + (14up^3 - 6upq - u^2 p) t^6/24
+// and f', g' by term-wise differentiation.  Used only when x = t max(sqrt u, |p|, sqrt|q|)
+// <= 2e-3, so the first omitted terms are below 1e-17 relative.  Returns false (state untouched)
+// when the interval is too long for the series.
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool drift_series(double mu, double t, double &x, double &y, double &z,
+                                             double &vx, double &vy, double &vz) {
+  const double r2 = fma(z, z, fma(y, y, x * x));
+  const double ri = rsqrt_fp64(r2);
+  const double ri2 = ri * ri;
+  const double u = mu * ri2 * ri;
+  const double p = fma(z, vz, fma(y, vy, x * vx)) * ri2;
+  const double q = fma(vz, vz, fma(vy, vy, vx * vx)) * ri2 - u;
+  const double t2 = t * t;
+  const double s = fmax(fmax(u, p * p), fabs(q)) * t2;
+  if (!(s <= 4e-6)) return false;
+  const double up = u * p, uq = u * q, u2 = u * u, p2 = p * p;
+  const double c4 = (3.0 * uq - 15.0 * up * p + u2) * (1.0 / 24.0);
+  const double c5 = (7.0 * up * p2 - 3.0 * up * q - u2 * p) * 0.125;
+  const double c6 = (-945.0 * up * p2 * p + 630.0 * up * p * q - 45.0 * uq * q + 210.0 * u2 * p2
+                     - 24.0 * u2 * q - u2 * u) * (1.0 / 720.0);
+  const double d5 = (9.0 * uq - 45.0 * up * p + u2) * (1.0 / 120.0);
+  const double d6 = (14.0 * up * p2 - 6.0 * up * q - u2 * p) * (1.0 / 24.0);
+  // f - 1, g - t, f', g' - 1 by Horner in t
+  const double fm1 = t2 * fma(t, fma(t, fma(t, fma(t, c6, c5), c4), 0.5 * up), -0.5 * u);
+  const double gmt = t2 * t * fma(t, fma(t, fma(t, d6, d5), 0.25 * up), -u * (1.0 / 6.0));
+  const double fd = t * fma(t, fma(t, fma(t, fma(t, 6.0 * c6, 5.0 * c5), 4.0 * c4), 1.5 * up), -u);
+  const double gdm1 = t2 * fma(t, fma(t, fma(t, 6.0 * d6, 5.0 * d5), up), -0.5 * u);
+  const double x0 = x, y0 = y, z0 = z;
+  x = fma(fm1, x0, fma(gmt, vx, fma(t, vx, x0)));
+  y = fma(fm1, y0, fma(gmt, vy, fma(t, vy, y0)));
+  z = fma(fm1, z0, fma(gmt, vz, fma(t, vz, z0)));
+  vx = fma(fd, x0, fma(gdm1, vx, vx));
+  vy = fma(fd, y0, fma(gdm1, vy, vy));
+  vz = fma(fd, z0, fma(gdm1, vz, vz));
+  return true;
+}
+
+// --------------------------------------------------------------------------------------------
+// host-side launch wrappers (defined in the kernel translation units)
+// --------------------------------------------------------------------------------------------
+struct LaunchCfg {
+  int sms;            // multiprocessors
+  int trap_blocks;    // persistent trapezoid grid
+  int rec_blocks;     // persistent recursion grid
+};
+
+void launch_setup_disk(const Dev &D, int d, cudaStream_t s);
+void launch_init_state(const Dev &D, int d, int n, const double *xh, const double *vh,
+                       const double *m, const double *rad, const double *rh, int compute_rh,
+                       cudaStream_t s);
+void launch_momentum(const Dev &D, int ndisks, cudaStream_t s);
+void launch_sundrift(const Dev &D, long long npart, int pre, cudaStream_t s);
+void launch_trap(const Dev &D, const LaunchCfg &L, int mode, int precision, cudaStream_t s);
+void launch_reduce(const Dev &D, long long npart, int precision, cudaStream_t s);
+void launch_split(const Dev &D, long long npart, cudaStream_t s);
+void launch_groups(const Dev &D, int ndisks, cudaStream_t s);
+void launch_drift(const Dev &D, long long npart, cudaStream_t s);
+void launch_recursion(const Dev &D, const LaunchCfg &L, cudaStream_t s);
+void launch_energy(const Dev &D, int d, const LaunchCfg &L, unsigned long long *acc /*4*(SA_NDIG+1)*/,
+                   cudaStream_t s);
+void launch_energy_round(unsigned long long *acc, double *out4, cudaStream_t s);
+void launch_gather_state(const Dev &D, int d, int n, double *x, double *v, double *m, double *rad,
+                         int *alive, cudaStream_t s);
+void launch_scatter_state(const Dev &D, int d, int n, const double *x, const double *v,
+                          cudaStream_t s);
+void launch_prologue(const Dev &D, int ndisks, cudaStream_t s);
+int trap_blocks_per_sm(int precision);
+int recursion_blocks_per_sm();
