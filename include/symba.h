@@ -178,6 +178,29 @@ void symba_pool_free(symba_pool *pool);
 /* Human-readable name of a status code. */
 const char *symba_status_string(int status);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Energy without device allocation.  The paper has no counterpart: this entry point exists    */
+/* for callers that cannot allocate device memory -- a host loop with a hard per-iteration      */
+/* latency budget (cudaMalloc and cudaFree may synchronise the device) or a process whose       */
+/* device memory belongs to another allocator (a framework's caching allocator, a fixed memory  */
+/* budget).  It computes the same E and L[3] as symba_energy, bit for bit, for n bodies given as */
+/* caller-owned DEVICE arrays: x (n x 3 heliocentric), v (n x 3 barycentric), m (n); out      */
+/* receives E, Lx, Ly, Lz (4 doubles, device).  Every body counts (pass only live ones); bodies */
+/* n_massive..n-1 are field particles.  Enqueued on cuda_stream (NULL = the legacy default      */
+/* stream); returns without waiting.                                                           */
+/* It calls no allocating routine: its exact-sum scratch is a 3,864-byte file-scope device     */
+/* array that every GPU which loads the library holds until the process exits.  The first call */
+/* on a device looks up that array's device address (once per device); make that first call   */
+/* before any stream capture.  All calls share the array and it keeps the last call's contents */
+/* (each call clears it first), so calls that overlap on the GPU -- on different streams, or   */
+/* from different host threads -- race and must be serialised by the caller.                   */
+/* Sizes: the scratch sums at most 2^31 - 1 terms, so n > SYMBA_ENERGY_STATIC_MAX_N is rejected */
+/* with SYMBA_E_INVAL, as are host pointers and n < 1.                                         */
+/* ---------------------------------------------------------------------------------------- */
+#define SYMBA_ENERGY_STATIC_MAX_N 65535
+int symba_energy_static(int n, int n_massive, const double *x, const double *v, const double *m,
+                        double G, double m0, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

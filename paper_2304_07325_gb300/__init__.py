@@ -29,13 +29,14 @@ SYMBA_E_NONFINITE = -7
 SYMBA_COLLISION = 1
 SYMBA_PRECISION_FP64 = 0
 SYMBA_PRECISION_MIXED = 1
+SYMBA_ENERGY_STATIC_MAX_N = 65535
 
 EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "symba_energy",
             "symba_enc_groups", "symba_get_state", "symba_set_state", "symba_get_stats",
             "symba_free", "symba_pool_create", "symba_pool_footprint", "symba_pool_admit",
             "symba_pool_step", "symba_pool_sync", "symba_pool_get_state", "symba_pool_energy",
             "symba_pool_get_stats", "symba_pool_evict", "symba_pool_free", "symba_status_string",
-            "symba_profile_step"]
+            "symba_profile_step", "symba_energy_static"]
 SYMBA_NPHASES = 10
 PHASES = ["sun drift + prologue", "kick 1 + encounter check", "kick-1 reduction", "grouping",
           "Kepler drift", "group recursion", "kick 2", "kick-2 reduction", "total momentum",
@@ -94,6 +95,7 @@ def lib():
             "symba_pool_free": (None, [vp]),
             "symba_status_string": (ctypes.c_char_p, [c_int]),
             "symba_profile_step": (c_int, [vp, c_int, dp]),
+            "symba_energy_static": (c_int, [c_int, c_int, vp, vp, vp, c_double, c_double, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
