@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+                    help="single: the N=10k headline; batched: 64 disks in one pool vs one at a time; "
+                         "serve: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--systems", type=int, default=64)
+    ap.add_argument("--n-lo", type=int, default=1000)
+    ap.add_argument("--n-hi", type=int, default=10000)
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--steps-cap", type=int, default=40)
     return ap.parse_args()
 
 
@@ -119,6 +127,17 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def reduce_max(value: float, device, world: int) -> float:
+    """The maximum of a per-rank value over all ranks (the timing rule: max over ranks)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload(args):
@@ -225,10 +244,7 @@ def run_ours(args):
     st = sysm.sync()
     if st < 0:
         raise RuntimeError(f"timed steps failed: {sy.status_string(st)}")
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = reduce_max(t_local, dev, world)
     units = 2.0 * P * args.steps * world
     value = units / t_max
 
@@ -249,10 +265,7 @@ def run_ours(args):
         sy.lib().symba_get_state(sysm._h, sy.c_void_p(xh.data_ptr()), sy.c_void_p(vh.data_ptr()),
                                  None, None, None)
     te = time.perf_counter() - te0
-    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    e2e_value = 2.0 * P * ne * world / float(te_t.item())
+    e2e_value = 2.0 * P * ne * world / reduce_max(te, dev, world)
 
     if rank == 0:
         peaks = measured_peaks()
@@ -293,10 +306,104 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Many independent disks (N log-uniform in [n_lo, n_hi], seeds 2000+k) stepped together in
+    one pool, against the same disks stepped one context at a time (FP64 both, or mixed for the
+    pool when --precision mixed).  Metric: simulation steps per second."""
+    import torch
+
+    import paper_2304_07325_gb300 as sy
+    from paper_2304_07325_gb300 import build, disk
+    from paper_2304_07325_gb300.serve import tiles_for
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sizes = disk.batch_sizes(args.systems, 2000, args.n_lo, args.n_hi)
+    disks = [disk.planetesimal_disk(n, 2000 + k) for k, n in enumerate(sizes)]
+    prec = sy.SYMBA_PRECISION_MIXED if args.precision == "mixed" else sy.SYMBA_PRECISION_FP64
+    tiles = sum(tiles_for(d.n, d.n_massive) for d in disks)
+    pool = sy.Pool(len(disks), sum(d.n for d in disks) + 32 * len(disks), tiles, prec)
+    for d in disks:
+        pool.admit(d.x, d.v, d.m, d.radius)
+    pool.step(args.warmup)
+    pool.sync()
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pool.step(1)
+        pool.sync()
+        step_ms.append(1e3 * (time.perf_counter() - t0))
+    clk = clocks.stop()
+    t_pool = sum(step_ms) / 1e3
+    pool.close()
+    # the same disks one context (one launch sequence) at a time, FP64
+    serial_steps = max(1, min(args.steps, 5))
+    t_serial = 0.0
+    for d in disks:
+        s1 = sy.System(d.x, d.v, d.m, d.radius)
+        s1.step(1)
+        s1.sync()
+        t0 = time.perf_counter()
+        s1.step(serial_steps)
+        s1.sync()
+        t_serial += time.perf_counter() - t0
+        s1.close()
+    pool_rate = len(disks) * args.steps / t_pool
+    serial_rate = len(disks) * serial_steps / t_serial
+    line = {"metric": "batched sim-steps/s", "value": pool_rate, "unit": "sim-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_pool / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f32-pair/f64-state", "data": "synthetic",
+            "config": {"workload": f"{len(disks)} planetesimal disks, N log-uniform {args.n_lo}-{args.n_hi} "
+                                   f"(seeds 2000+k), all massive, dt=0.5 yr, M=4, one pool",
+                       "sizes": sizes},
+            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+            "serial_fp64_one_at_a_time": {"value": serial_rate, "unit": "sim-steps/s", "steps_each": serial_steps},
+            "speedup_vs_serial": pool_rate / serial_rate, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson request stream (mean 20/s; N log-uniform, step budgets capped for a bounded run)
+    through the continuous-batching server; mixed-precision kick, FP64 drifts."""
+    import torch
+
+    import paper_2304_07325_gb300 as sy
+    from paper_2304_07325_gb300 import build
+    from paper_2304_07325_gb300.serve import Server, poisson_requests, tiles_for
+    build.build()
+    torch.cuda.set_device(0)
+    prec = sy.SYMBA_PRECISION_FP64 if args.precision == "fp64" else sy.SYMBA_PRECISION_MIXED
+    reqs = poisson_requests(args.requests, 20.0, 3000, args.n_lo, args.n_hi, 100, 5000,
+                            steps_cap=args.steps_cap)
+    max_n = max(len(r.m) for r in reqs)
+    srv = Server(max_systems=32, max_particles=32 * (max_n + 32), max_tiles=16 * tiles_for(max_n, max_n),
+                 precision=prec, hbm_budget_bytes=64 << 30)
+    results, stats = srv.run(reqs, keep_state=False)
+    srv.close()
+    summ = stats.summary()
+    line = {"metric": "served sim-steps/s", "value": summ["sim_steps_per_s"], "unit": "sim-steps/s",
+            "n_gpus": 1, "steps": summ["pool_steps"], "warmup": 0, "ms_per_step": summ["p50_step_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-pair/f64-state" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.requests} Poisson requests (20/s), N log-uniform {args.n_lo}-{args.n_hi}, "
+                                   f"step budgets U[100,5000] capped at {args.steps_cap}"},
+            "p50_step_ms": summ["p50_step_ms"], "p99_step_ms": summ["p99_step_ms"],
+            "max_resident": summ["max_resident"], "completed": len(results), "wall_s": summ["wall_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

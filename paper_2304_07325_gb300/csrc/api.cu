@@ -337,6 +337,9 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   A(&D.gpi, pc); A(&D.gpj, pc); A(&D.lev, pc); A(&D.tmpj, pc);
   A(&D.perm, pc); A(&D.ptmp, pc); A(&D.pR0, pc); A(&D.pinvR0, pc);
   A(&D.mperm, n); A(&D.mtmp, n);
+  A(&D.gx, n); A(&D.gy, n); A(&D.gz, n); A(&D.gvx, n); A(&D.gvy, n); A(&D.gvz, n);
+  A(&D.gmm, n); A(&D.ggm, n); A(&D.grad, n); A(&D.grh, n); A(&D.galive, n);
+  A(&D.gpa, pc); A(&D.gpb, pc);
   A(&D.pf, 5 * pc); A(&D.adj, 2 * pc);
   A(&D.cnt, n); A(&D.start, n); A(&D.cursor, n); A(&D.parent, n); A(&D.inpair, n);
   A(&D.gidx, n); A(&D.mslot, n); A(&D.adj_off, n); A(&D.adj_cnt, n);
@@ -588,9 +591,9 @@ long long symba_pool_footprint(int n, int n_massive, const symba_params *p) {
   if (n < 1 || n_massive < 0 || n_massive > n) return -1;
   const long long nb = (n + SYM_TILE - 1) / SYM_TILE, nbm = (n_massive + SYM_TILE - 1) / SYM_TILE;
   const long long np = nb * SYM_TILE;
-  const long long per_particle = 10 * 8 + 2 * 4 + 11 * 4 + 12 * 4 + 3 * 8 + 6 * 4 / 2 + 4;
+  const long long per_particle = 20 * 8 + 3 * 4 + 12 * 4 + 12 * 4 + 3 * 8 + 6 * 4 / 2 + 4;
   const long long pairs = default_pair_cap(p, n);
-  const long long per_pair = 11 * 4 + 7 * 8 + 2 * 4;
+  const long long per_pair = 13 * 4 + 7 * 8 + 2 * 4;
   return np * per_particle + pairs * per_pair + tiles_of((int)nb, (int)nbm) * (16 + 2 * 3 * 32 * 8);
 }
 

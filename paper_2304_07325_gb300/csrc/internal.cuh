@@ -62,6 +62,10 @@ struct Dev {
   int *perm, *ptmp;             // nested active-pair lists of the recursion (per grouped pair)
   double *pR0, *pinvR0;         // level-0 critical radius of each grouped pair and its inverse
   int *mperm, *mtmp;            // nested active-member lists (per member slot)
+  // member-slot copies of the bodies of large groups (indexed like gmem)
+  double *gx, *gy, *gz, *gvx, *gvy, *gvz, *gmm, *ggm, *grad, *grh;
+  int *galive;
+  int *gpa, *gpb;               // grouped pair -> member slots (large groups)
   double *pf;                   // [pair][5] per-pair force scratch (d, fi, fj)
   int *adj;                     // [2 * pair] adjacency: (grouped pair index << 1) | side
   // particle-indexed scratch for grouping
@@ -131,6 +135,20 @@ __device__ __forceinline__ double rsqrt_fp64(double r2) {
   return rsqrt(r2);
 }
 
+// Order of non-negative doubles through their bit patterns (an integer comparison instead of an
+// FP64-pipe one; valid for +0, finite and +inf operands).
+__device__ __forceinline__ bool lt_nn(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool is_neg(double a) { return __double_as_longlong(a) < 0; }
+__device__ __forceinline__ double neg(double a) {
+  return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ double abs_bits(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double max_nn(double a, double b) { return lt_nn(a, b) ? b : a; }
+
 // Select without arithmetic: v if keep, else 0.0 (integer select on the bit pattern).
 __device__ __forceinline__ double keep_or_zero(double v, bool keep) {
   long long b = __double_as_longlong(v);
@@ -166,8 +184,8 @@ __device__ __forceinline__ double binom_d(int n, int k) {
 }
 
 __device__ __forceinline__ double partition_fn(double x, int l) {
-  if (x <= 0.0) return 0.0;
-  if (x >= 1.0) return 1.0;
+  if (__double_as_longlong(x) <= 0ll) return 0.0;             // x <= 0 (or -0)
+  if (!lt_nn(x, 1.0)) return 1.0;                             // x >= 1
   if (l == 3) {
     // x^4 (35 - 84 x + 70 x^2 - 20 x^3)
     const double x2 = x * x;
@@ -423,8 +441,9 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
 //       + (-945up^4 + 630up^2 q - 45uq^2 + 210u^2p^2 - 24u^2 q - u^3) t^6/720
 //   g = t - u t^3/6 + u p t^4/4 + (9uq - 45up^2 + u^2) t^5/120 + (14up^3 - 6upq - u^2 p) t^6/24
 // and f', g' by term-wise differentiation.  Used only when x = t max(sqrt u, |p|, sqrt|q|)
-// <= 2e-3, so the first omitted terms are below 1e-17 relative.  Returns false (state untouched)
-// when the interval is too long for the series.
+// <= 2e-3, so the first omitted terms are below 1e-17 relative; for x < 3.2e-5 the series stops
+// after t^3 and for x < 1e-6 after t^2 (the omitted terms are then below 1.1e-18).  Returns false
+// (state untouched) when the interval is too long for the series.
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool drift_series(double mu, double t, double &x, double &y, double &z,
                                              double &vx, double &vy, double &vz) {
@@ -433,23 +452,40 @@ __device__ __forceinline__ bool drift_series(double mu, double t, double &x, dou
   const double ri2 = ri * ri;
   const double u = mu * ri2 * ri;
   const double p = fma(z, vz, fma(y, vy, x * vx)) * ri2;
-  const double q = fma(vz, vz, fma(vy, vy, vx * vx)) * ri2 - u;
+  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+  const double q = fma(v2, ri2, -u);
   const double t2 = t * t;
-  const double s = fmax(fmax(u, p * p), fabs(q)) * t2;
-  if (!(s <= 4e-6)) return false;
-  const double up = u * p, uq = u * q, u2 = u * u, p2 = p * p;
-  const double c4 = (3.0 * uq - 15.0 * up * p + u2) * (1.0 / 24.0);
-  const double c5 = (7.0 * up * p2 - 3.0 * up * q - u2 * p) * 0.125;
-  const double c6 = (-945.0 * up * p2 * p + 630.0 * up * p * q - 45.0 * uq * q + 210.0 * u2 * p2
-                     - 24.0 * u2 * q - u2 * u) * (1.0 / 720.0);
-  const double d5 = (9.0 * uq - 45.0 * up * p + u2) * (1.0 / 120.0);
-  const double d6 = (14.0 * up * p2 - 6.0 * up * q - u2 * p) * (1.0 / 24.0);
-  // f - 1, g - t, f', g' - 1 by Horner in t
-  const double fm1 = t2 * fma(t, fma(t, fma(t, fma(t, c6, c5), c4), 0.5 * up), -0.5 * u);
-  const double gmt = t2 * t * fma(t, fma(t, fma(t, d6, d5), 0.25 * up), -u * (1.0 / 6.0));
-  const double fd = t * fma(t, fma(t, fma(t, fma(t, 6.0 * c6, 5.0 * c5), 4.0 * c4), 1.5 * up), -u);
-  const double gdm1 = t2 * fma(t, fma(t, fma(t, 6.0 * d6, 5.0 * d5), up), -0.5 * u);
+  // x^2 = s bounds the size of the first term of the series relative to 1
+  const double s = max_nn(max_nn(u, p * p), abs_bits(q)) * t2;
+  if (!lt_nn(s, 4.0000000000000001e-6)) return false;
   const double x0 = x, y0 = y, z0 = z;
+  double fm1, gmt, fd, gdm1;
+  if (lt_nn(s, 1e-12)) {
+    // x < 1e-6: terms of order x^3 and beyond are below 1e-18
+    fm1 = t2 * (-0.5 * u);
+    gmt = 0.0;
+    fd = -u * t;
+    gdm1 = fm1;
+  } else if (lt_nn(s, 1e-9)) {
+    // x < 3.2e-5: terms of order x^4 and beyond are below 1.1e-18
+    const double up = u * p;
+    fm1 = t2 * fma(t, 0.5 * up, -0.5 * u);
+    gmt = t2 * t * (-u * (1.0 / 6.0));
+    fd = t * fma(t, 1.5 * up, -u);
+    gdm1 = t2 * fma(t, up, -0.5 * u);
+  } else {
+    const double up = u * p, uq = u * q, u2 = u * u, p2 = p * p;
+    const double c4 = (3.0 * uq - 15.0 * up * p + u2) * (1.0 / 24.0);
+    const double c5 = (7.0 * up * p2 - 3.0 * up * q - u2 * p) * 0.125;
+    const double c6 = (-945.0 * up * p2 * p + 630.0 * up * p * q - 45.0 * uq * q + 210.0 * u2 * p2
+                       - 24.0 * u2 * q - u2 * u) * (1.0 / 720.0);
+    const double d5 = (9.0 * uq - 45.0 * up * p + u2) * (1.0 / 120.0);
+    const double d6 = (14.0 * up * p2 - 6.0 * up * q - u2 * p) * (1.0 / 24.0);
+    fm1 = t2 * fma(t, fma(t, fma(t, fma(t, c6, c5), c4), 0.5 * up), -0.5 * u);
+    gmt = t2 * t * fma(t, fma(t, fma(t, d6, d5), 0.25 * up), -u * (1.0 / 6.0));
+    fd = t * fma(t, fma(t, fma(t, fma(t, 6.0 * c6, 5.0 * c5), 4.0 * c4), 1.5 * up), -u);
+    gdm1 = t2 * fma(t, fma(t, fma(t, 6.0 * d6, 5.0 * d5), up), -0.5 * u);
+  }
   x = fma(fm1, x0, fma(gmt, vx, fma(t, vx, x0)));
   y = fma(fm1, y0, fma(gmt, vy, fma(t, vy, y0)));
   z = fma(fm1, z0, fma(gmt, vz, fma(t, vz, z0)));

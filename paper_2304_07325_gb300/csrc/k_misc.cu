@@ -228,26 +228,29 @@ __global__ void k_reduce(Dev D, long long npart) {
     const int li = (int)p - dd.off;
     if (li >= dd.n || !D.alive[p]) continue;
     const int B = li >> 5, lane = li & 31;
-    // four interleaved partial sums (term index mod 4), combined in a fixed order
-    double a4[4][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-    int term = 0;
-    if (B < dd.nbm) {
-      const int t0 = row_start(dd, B);
-      for (int J = B; J < dd.nb; ++J, ++term) {
-        const double *pp = D.part + ((size_t)(t0 + (J - B)) * 2 * 3) * 32 + lane;
-        double *a = a4[term & 3];
-        a[0] += pp[0]; a[1] += pp[32]; a[2] += pp[64];
-      }
-    }
+    // the partials of p in a fixed order (its row, then its column), as a list of tile slots;
+    // two interleaved sums (even and odd terms) keep two loads in flight, combined at the end
+    const int nrow = B < dd.nbm ? dd.nb - B : 0;
     const int Imax = B < dd.nbm ? B : dd.nbm;
-    for (int I = 0; I < Imax; ++I, ++term) {
-      const double *pp = D.part + (((size_t)(row_start(dd, I) + (B - I)) * 2 + 1) * 3) * 32 + lane;
-      double *a = a4[term & 3];
-      a[0] += pp[0]; a[1] += pp[32]; a[2] += pp[64];
+    const int nterm = nrow + Imax;
+    const int t0 = nrow ? row_start(dd, B) : 0;
+    auto slot = [&](int q) -> const double * {
+      if (q < nrow) return D.part + ((size_t)(t0 + q) * 2 * 3) * 32 + lane;
+      const int I = q - nrow;
+      return D.part + (((size_t)(row_start(dd, I) + (B - I)) * 2 + 1) * 3) * 32 + lane;
+    };
+    double ax0 = 0.0, ay0 = 0.0, az0 = 0.0, ax1 = 0.0, ay1 = 0.0, az1 = 0.0;
+    int q = 0;
+    for (; q + 1 < nterm; q += 2) {
+      const double *p0 = slot(q), *p1 = slot(q + 1);
+      ax0 += p0[0]; ay0 += p0[32]; az0 += p0[64];
+      ax1 += p1[0]; ay1 += p1[32]; az1 += p1[64];
     }
-    const double ax = (a4[0][0] + a4[1][0]) + (a4[2][0] + a4[3][0]);
-    const double ay = (a4[0][1] + a4[1][1]) + (a4[2][1] + a4[3][1]);
-    const double az = (a4[0][2] + a4[1][2]) + (a4[2][2] + a4[3][2]);
+    if (q < nterm) {
+      const double *p0 = slot(q);
+      ax0 += p0[0]; ay0 += p0[32]; az0 += p0[64];
+    }
+    const double ax = ax0 + ax1, ay = ay0 + ay1, az = az0 + az1;
     const double h = 0.5 * dd.dt;
     D.vx[p] = __dadd_rn(D.vx[p], __dmul_rn(h, ax));
     D.vy[p] = __dadd_rn(D.vy[p], __dmul_rn(h, ay));

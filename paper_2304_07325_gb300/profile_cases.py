@@ -1,0 +1,48 @@
+"""Small, self-contained workloads for profiling single kernels (ncu, CUDA events).
+
+    python -m paper_2304_07325_gb300.profile_cases step --n 10000 [--precision mixed]
+        one step of the Sec. 3 disk; the trapezoid kicks (k_trap_*) run twice
+    python -m paper_2304_07325_gb300.profile_cases bound_pair [--steps 1]
+        one step of a 5-body encounter group of the 10,000-body disk (seed 1002) that holds a
+        bound pair: the group recursion (k_recursion) dominates, ~34,000 sub-steps per step
+
+Each case prints the per-phase device times measured with CUDA events (symba_profile_step).
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import PHASES, SYMBA_PRECISION_FP64, SYMBA_PRECISION_MIXED, System, default_params, disk
+
+BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["step", "bound_pair"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--seed", type=int, default=1002)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    a = ap.parse_args(argv)
+    prec = SYMBA_PRECISION_MIXED if a.precision == "mixed" else SYMBA_PRECISION_FP64
+    d = disk.planetesimal_disk(a.n if a.case == "step" else 10000, a.seed)
+    if a.case == "bound_pair":
+        g = BOUND_PAIR_GROUP
+        s = System(d.x[g], d.v[g], d.m[g], d.radius[g], params=default_params(precision=prec))
+    else:
+        s = System(d.x, d.v, d.m, d.radius, params=default_params(precision=prec))
+    ph = s.profile_step(a.steps)
+    st = s.stats()
+    status = s.sync()
+    print(f"case {a.case} status {status} substeps {st.substeps} depth {st.max_depth}")
+    for name, ms in zip(PHASES, ph):
+        print(f"  {name:28s} {ms:10.3f} ms")
+    if st.substeps:
+        print(f"  recursion per sub-step      {1e3 * ph[5] / st.substeps:10.3f} us")
+    s.close()
+    return 0 if status >= 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
