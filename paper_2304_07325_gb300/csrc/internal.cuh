@@ -442,31 +442,53 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
 //   g = t - u t^3/6 + u p t^4/4 + (9uq - 45up^2 + u^2) t^5/120 + (14up^3 - 6upq - u^2 p) t^6/24
 // and f', g' by term-wise differentiation.  Used only when x = t max(sqrt u, |p|, sqrt|q|)
 // <= 2e-3, so the first omitted terms are below 1e-17 relative; for x < 3.2e-5 the series stops
-// after t^3 and for x < 1e-6 after t^2 (the omitted terms are then below 1.1e-18).  Returns false
+// after t^3 and for x < 1e-6 after t^2 (the omitted terms are then below 1.1e-18).  The order is
+// chosen from an FP32 estimate of s = x^2 with a factor-2 margin on each threshold.  Returns false
 // (state untouched) when the interval is too long for the series.
 // --------------------------------------------------------------------------------------------
+__device__ __forceinline__ float f32_trunc(double a) {
+  // FP64 -> FP32 by bit manipulation (truncation; no FP64-pipe conversion); for |a| in the normal
+  // FP32 range, relative error < 2^-23, which the order decision below leaves margin for
+  const long long b = __double_as_longlong(a);
+  const int e = (int)((b >> 52) & 0x7FF) - 896;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(((int)(b >> 32) & 0x80000000) | 0x7F800000);
+  return __int_as_float(((int)(b >> 32) & 0x80000000) | (e << 23) | (int)((b >> 29) & 0x7FFFFF));
+}
+
 __device__ __forceinline__ bool drift_series(double mu, double t, double &x, double &y, double &z,
                                              double &vx, double &vy, double &vz) {
+  // order decision in FP32 (2x margin on every threshold): s = x^2 bounds the first term
+  const float xf = f32_trunc(x), yf = f32_trunc(y), zf = f32_trunc(z);
+  const float vxf = f32_trunc(vx), vyf = f32_trunc(vy), vzf = f32_trunc(vz);
+  const float r2f = fmaf(zf, zf, fmaf(yf, yf, xf * xf));
+  const float rif = rsqrtf(r2f), ri2f = rif * rif;
+  const float uf = f32_trunc(mu) * ri2f * rif;
+  const float pf = fmaf(zf, vzf, fmaf(yf, vyf, xf * vxf)) * ri2f;
+  const float qf = fmaf(fmaf(vzf, vzf, fmaf(vyf, vyf, vxf * vxf)), ri2f, -uf);
+  const float tf = f32_trunc(t);
+  const float sf = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * tf * tf;
+  if (!(sf <= 2.0e-6f)) return false;
   const double r2 = fma(z, z, fma(y, y, x * x));
   const double ri = rsqrt_fp64(r2);
   const double ri2 = ri * ri;
   const double u = mu * ri2 * ri;
-  const double p = fma(z, vz, fma(y, vy, x * vx)) * ri2;
-  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
-  const double q = fma(v2, ri2, -u);
   const double t2 = t * t;
-  // x^2 = s bounds the size of the first term of the series relative to 1
-  const double s = max_nn(max_nn(u, p * p), abs_bits(q)) * t2;
-  if (!lt_nn(s, 4.0000000000000001e-6)) return false;
   const double x0 = x, y0 = y, z0 = z;
-  double fm1, gmt, fd, gdm1;
-  if (lt_nn(s, 1e-12)) {
+  if (sf < 5e-13f) {
     // x < 1e-6: terms of order x^3 and beyond are below 1e-18
-    fm1 = t2 * (-0.5 * u);
-    gmt = 0.0;
-    fd = -u * t;
-    gdm1 = fm1;
-  } else if (lt_nn(s, 1e-9)) {
+    const double fm1 = t2 * (-0.5 * u), fd = -u * t;
+    x = fma(fm1, x0, fma(t, vx, x0));
+    y = fma(fm1, y0, fma(t, vy, y0));
+    z = fma(fm1, z0, fma(t, vz, z0));
+    vx = fma(fd, x0, fma(fm1, vx, vx));
+    vy = fma(fd, y0, fma(fm1, vy, vy));
+    vz = fma(fd, z0, fma(fm1, vz, vz));
+    return true;
+  }
+  const double p = fma(z, vz, fma(y, vy, x * vx)) * ri2;
+  double fm1, gmt, fd, gdm1;
+  if (sf < 5e-10f) {
     // x < 3.2e-5: terms of order x^4 and beyond are below 1.1e-18
     const double up = u * p;
     fm1 = t2 * fma(t, 0.5 * up, -0.5 * u);
@@ -474,6 +496,8 @@ __device__ __forceinline__ bool drift_series(double mu, double t, double &x, dou
     fd = t * fma(t, 1.5 * up, -u);
     gdm1 = t2 * fma(t, up, -0.5 * u);
   } else {
+    const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+    const double q = fma(v2, ri2, -u);
     const double up = u * p, uq = u * q, u2 = u * u, p2 = p * p;
     const double c4 = (3.0 * uq - 15.0 * up * p + u2) * (1.0 / 24.0);
     const double c5 = (7.0 * up * p2 - 3.0 * up * q - u2 * p) * 0.125;

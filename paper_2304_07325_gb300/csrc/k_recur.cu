@@ -400,12 +400,18 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
     ib = D.mslot[D.gpj[C.poff + lane]];
     lev = 0;
   }
-  double R0, iR0;
-  {
+  // per-pair constants: critical radius R_0, 1/R_0, R_0^2 and the contact prefilter threshold
+  double R0, iR0, R0sq, Rcut;
+  auto pair_consts = [&]() {
     const double ra = SH(rh, ia), rb = SH(rh, ib);
+    const double sa = SH(rad, ia), sb = SH(rad, ib);
     R0 = __dmul_rn(C.lam, __dadd_rn(ra, rb));
     iR0 = R0 > 0.0 ? 1.0 / R0 : 0.0;
-  }
+    R0sq = R0 * R0;
+    const double Rc = sa + sb;
+    Rcut = 1.0000001 * (Rc * Rc);
+  };
+  pair_consts();
   unsigned im = 0u, jm = 0u;
   for (int q = 0; q < np; ++q) {
     const int a_ = SH(ia, q), b_ = SH(ib, q);
@@ -475,17 +481,16 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
     const double xa = SH(x, ia), ya = SH(y, ia), za = SH(z, ia);
     const double xb = SH(x, ib), yb = SH(y, ib), zb = SH(z, ib);
     const int aa = SH(alive, ia), ab = SH(alive, ib);
-    const double rda = SH(rad, ia), rdb = SH(rad, ib);
     const double dx = xb - xa, dy = yb - ya, dz = zb - za;
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     const bool both = inL && aa && ab;
-    const double Rc = rda + rdb;
-    bool ct = both && lt_nn(r2, 1.0000001 * (Rc * Rc)) && contact_regs(xa, ya, za, xb, yb, zb, rda, rdb);
+    const double rda = SH(rad, ia), rdb = SH(rad, ib);
+    const bool ct = both && lt_nn(r2, Rcut) && contact_regs(xa, ya, za, xb, yb, zb, rda, rdb);
     if (!__any_sync(FULL, ct)) {
       const double vxa = SH(vx, ia), vya = SH(vy, ia), vza = SH(vz, ia);
       const double vxb = SH(vx, ib), vyb = SH(vy, ib), vzb = SH(vz, ib);
       bool fl = false;
-      if (both) fl = predicate_regs(dx, dy, dz, r2, vxb - vxa, vyb - vya, vzb - vza, R0 * R0 * C.dp->ck2[k], h);
+      if (both) fl = predicate_regs(dx, dy, dz, r2, vxb - vxa, vyb - vya, vzb - vza, R0sq * C.dp->ck2[k], h);
       if (inL) lev = fl ? k : k - 1;
       *merged = false;
       return __any_sync(FULL, fl) != 0;
@@ -521,10 +526,8 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
           }
           if (lane == b_) { m = 0.0; gm = 0.0; rad = 0.0; rh = 0.0; alive = 0; }
           if (lane == 0) atomicAdd(&D.stat[C.d].merges, 1ull);
-          // critical radii follow the new Hill radius
-          const double ra2 = SH(rh, ia), rb2 = SH(rh, ib);
-          R0 = __dmul_rn(C.lam, __dadd_rn(ra2, rb2));
-          iR0 = R0 > 0.0 ? 1.0 / R0 : 0.0;
+          // critical radii and contact thresholds follow the new body
+          pair_consts();
         } else {
           const double R0q = SH(R0, q);
           fl = predicate_regs(xb_ - xa_, yb_ - ya_, zb_ - za_,

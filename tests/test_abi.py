@@ -61,3 +61,25 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(sy, "_lib", None)
     with pytest.raises(RuntimeError):
         sy.lib()
+
+
+def test_invalid_arguments_are_rejected_before_any_device_call(built_lib):
+    import ctypes as C
+
+    import numpy as np
+
+    import paper_2304_07325_gb300 as sy
+    lib = sy.lib()
+    p = sy.default_params()
+    h = C.c_void_p()
+    x = np.zeros((4, 3))
+    ptr = lambda a: C.c_void_p(a.ctypes.data)
+    m = np.zeros(4)
+    # n < 1, n_massive > n, NULL params
+    assert lib.symba_init(C.byref(h), C.byref(p), 0, 0, ptr(x), ptr(x), ptr(m), ptr(m), None, None) == sy.SYMBA_E_INVAL
+    assert lib.symba_init(C.byref(h), C.byref(p), 4, 5, ptr(x), ptr(x), ptr(m), ptr(m), None, None) == sy.SYMBA_E_INVAL
+    assert lib.symba_init(C.byref(h), None, 4, 4, ptr(x), ptr(x), ptr(m), ptr(m), None, None) == sy.SYMBA_E_INVAL
+    assert lib.symba_step(None, 1) == sy.SYMBA_E_INVAL
+    assert lib.symba_energy_static(0, 0, None, None, None, 1.0, 1.0, None, None) == sy.SYMBA_E_INVAL
+    assert lib.symba_pool_create(C.byref(h), 0, 10, 10, 0, None) == sy.SYMBA_E_INVAL
+    assert lib.symba_pool_create(C.byref(h), 1, 10, 10, 7, None) == sy.SYMBA_E_INVAL
