@@ -233,15 +233,21 @@ def run_ours(args):
     clocks.start()
     t_wall0 = time.perf_counter()
     depth_max, substeps = 0, 0
+    chain_us = []                              # recursion time per sub-step of the longest chain
+    chain_max = 0
     for k in range(args.steps):
         if flush is not None:
             flush.fill_(float(k))
         starts[k].record(stream)
-        phase_tot += sysm.profile_step(1)      # events between the step's kernels, same stream
+        ph = sysm.profile_step(1)              # events between the step's kernels, same stream
         ends[k].record(stream)
+        phase_tot += ph
         s = sysm.stats()
         depth_max = max(depth_max, s.max_depth)
         substeps += s.substeps
+        chain_max = max(chain_max, s.max_chain)
+        if s.max_chain > 0:
+            chain_us.append(1e3 * ph[5] / s.max_chain)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -310,7 +316,8 @@ def run_ours(args):
                 "steps_per_s": args.steps * world / t_max,
                 "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "phase_ms_per_step": phases, "max_depth": depth_max,
-                "substeps_per_step": substeps / args.steps,
+                "substeps_per_step": substeps / args.steps, "longest_chain_substeps": chain_max,
+                "us_per_chain_substep_median": statistics.median(chain_us) if chain_us else None,
                 "roofline": roofline, "roofline_kick": roofline_kick, "cpu_baseline": cb,
                 "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
                         "h2d_bytes_per_step": 2 * 8 * 3 * ntot, "d2h_bytes_per_step": 2 * 8 * 3 * ntot,

@@ -71,6 +71,8 @@ typedef struct {
   long long merges;         /* mergers since the context was created */
   long long substeps;       /* recursion sub-steps (E_k calls, k >= 1) during the last call */
   long long steps;          /* steps taken since the context was created */
+  long long max_chain;      /* most sub-steps of one group in one step during the last call: the
+                               dependent chain that bounds the recursion's time */
 } symba_stats;
 
 typedef struct symba_ctx symba_ctx;

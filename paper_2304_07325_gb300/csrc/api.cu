@@ -214,6 +214,7 @@ __global__ void k_reset_call(DiskStat *st, int nd) {
   for (int d = threadIdx.x; d < nd; d += blockDim.x) {
     st[d].max_depth = 0;
     st[d].substeps = 0;
+    st[d].max_chain = 0;
   }
 }
 
@@ -545,6 +546,7 @@ int get_stats(symba_pool *P, int d, symba_stats *out) {
   out->status = st.status;
   out->merges = (long long)st.merges;
   out->substeps = (long long)st.substeps;
+  out->max_chain = (long long)st.max_chain;
   out->steps = 0;
   return SYMBA_OK;
 }

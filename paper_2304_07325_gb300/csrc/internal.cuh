@@ -32,6 +32,7 @@ struct DiskDesc {
 struct DiskStat {               // mutable per-system counters (device)
   int npairs, ngroups, status, max_depth;
   unsigned long long merges, substeps, merges_reported;
+  unsigned long long max_chain;   // most sub-steps of one group in one step
 };
 
 struct Dev {
@@ -133,6 +134,22 @@ __device__ __forceinline__ double rsqrt_fp64(double r2) {
     return fma(y0 * e, fma(e, 0.375, 0.5), y0);
   }
   return rsqrt(r2);
+}
+
+// The FP32 seed of rsqrt_fp64 alone: built from the bits of r2 and widened back to FP64 by bit
+// operations; false (y0 untouched) when r2 is outside the normal FP32 range.
+__device__ __forceinline__ bool rsqrt_seed(double r2, double &y0) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int fe = ((hi >> 20) & 0x7FF) - 896;
+  if (!((unsigned)(fe - 1) <= 253u && hi > 0)) return false;
+  const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+  float y0f;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(((unsigned)fe << 23) | m23)));
+  const unsigned yb = __float_as_uint(y0f);
+  const int ye = (int)((yb >> 23) & 0xFF) + 896;
+  y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
+  return true;
 }
 
 // Order of non-negative doubles through their bit patterns (an integer comparison instead of an

@@ -23,6 +23,7 @@ __global__ void k_setup_disk(Dev D, int d) {
   st->max_depth = 0;
   st->merges = 0;
   st->substeps = 0;
+  st->max_chain = 0;
   st->merges_reported = 0;
 }
 

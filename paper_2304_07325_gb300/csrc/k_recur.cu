@@ -51,9 +51,14 @@ struct SmallView {             // shared-memory backing of a small group
 struct GroupCtx {
   int d, moff, mcnt, poff, pcnt;
   int M, l, max_depth, max_substeps;
-  double dt, lam, G, mu;
+  double dt, lam, G, mu, invM;
   const DiskDesc *dp;
 };
+
+// h / M; for M a power of two the product with 1/M is the same number without a division
+__device__ __forceinline__ double sub_interval(const GroupCtx &C, double h) {
+  return (C.M & (C.M - 1)) == 0 ? h * C.invM : h / (double)C.M;
+}
 
 __device__ __forceinline__ bool contact(const GView &S, int a, int b) {
   const double dx = __dsub_rn(S.x[b], S.x[a]), dy = __dsub_rn(S.y[b], S.y[a]), dz = __dsub_rn(S.z[b], S.z[a]);
@@ -328,7 +333,7 @@ __device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const L
       drift_range(S, C, D, lm1, V.lenM[k], V.h[k], lane);
       if (deeper) {
         ++k;
-        V.h[k] = V.h[k - 1] / (double)C.M;
+        V.h[k] = sub_interval(C, V.h[k - 1]);
         V.cnt[k] = 0;
         continue;
       }
@@ -347,6 +352,7 @@ __device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const L
   if (lane == 0) {
     atomicMax(&D.stat[C.d].max_depth, deepest);
     atomicAdd(&D.stat[C.d].substeps, (unsigned long long)substeps);
+    atomicMax(&D.stat[C.d].max_chain, (unsigned long long)substeps);
   }
 }
 
@@ -377,7 +383,309 @@ __device__ __forceinline__ bool predicate_regs(double dx, double dy, double dz, 
   return is_neg(e) || lt_nn(e, R2);
 }
 
-__device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double *hs, int *cs) {
+// --------------------------------------------------------------------------------------------
+// One pair alone below level k (F_{k-1} = {q}): every sub-step of levels >= k then touches only
+// the pair's two bodies, and a group spends most of its sub-steps there when it holds a close or
+// bound pair.  The sub-step chain is latency-bound: GB300 runs one FP64 warp instruction per ~64
+// cycles whatever the number of active lanes, and an FP64 result that passes through another
+// unit (shuffle, select, integer compare) before the next FP64 instruction costs ~46 cycles more.
+// So the warp holds the two bodies component-wise -- lane = 8 cp + 4 b + c: copy cp (0..3) of
+// body b (0, 1), component c (x, y, z, and a zero pad) -- which makes
+//   - a vector update one FP64 instruction for all components of both bodies;
+//   - a sum over components one gather (three shuffles) and two additions, in the order
+//     (x + y) + z;
+//   - three or four independent operations of a scalar chain one fused multiply-add, copy cp
+//     taking the cp-th operands (branch-free bit selects), the results exchanged by shuffles.
+// Levels whose shell weight vanishes for the current separation (outside [R_{j+1}, R_{j-1}))
+// skip the force and the kick.  The method is the general path's, step by step; the arithmetic
+// differs only in rounding (component sums, the weight argument r A + B with per-level
+// constants, Estrin's form of f_3, the series coefficients).
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ double fma_rn(double a, double b, double c) {
+  double r;
+  asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
+  return r;
+}
+// a where the mask is set, b elsewhere (one bit-select per 32-bit half, no branch)
+__device__ __forceinline__ double bsel(double a, double b, unsigned m) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const unsigned lo = ((unsigned)ia & m) | ((unsigned)ib & ~m);
+  const unsigned hi = ((unsigned)(ia >> 32) & m) | ((unsigned)(ib >> 32) & ~m);
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+// four independent fused multiply-adds in one instruction: copy cp evaluates a_cp b_cp + c_cp
+// (m0, m1: the bits of cp as masks; a product is a fused multiply-add with -0, which returns it
+// exactly, signed zeros included)
+__device__ __forceinline__ double fma4(unsigned m0, unsigned m1, double a0, double b0, double c0,
+                                       double a1, double b1, double c1, double a2, double b2,
+                                       double c2, double a3, double b3, double c3) {
+  const double a = bsel(bsel(a3, a2, m0), bsel(a1, a0, m0), m1);
+  const double b = bsel(bsel(b3, b2, m0), bsel(b1, b0, m0), m1);
+  const double c = bsel(bsel(c3, c2, m0), bsel(c1, c0, m0), m1);
+  return fma_rn(a, b, c);
+}
+// the value copy k holds for this lane's body and component
+__device__ __forceinline__ double cpy(double v, int lane, int k) {
+  return __shfl_sync(FULL, v, (lane & 7) | (k << 3));
+}
+// (p_x + p_y) + p_z over the component lanes of this lane's body (base: its x lane)
+__device__ __forceinline__ double csum3(double p, int base) {
+  const double a = __shfl_sync(FULL, p, base), b = __shfl_sync(FULL, p, base + 1);
+  const double c = __shfl_sync(FULL, p, base + 2);
+  return (a + b) + c;
+}
+// The FP32 seed of 1/sqrt(r2) widened to FP64 (y0) and its exact square (t = y0^2, from the
+// 24-bit significand by an integer product), both without the FP64 pipe; false outside the
+// normal FP32 range.
+__device__ __forceinline__ bool rsqrt_seed_sq(double r2, double &y0, double &t) {
+  const int hi = __double2hiint(r2);
+  const unsigned lo = (unsigned)__double2loint(r2);
+  const int fe = ((hi >> 20) & 0x7FF) - 896;
+  if (!((unsigned)(fe - 1) <= 253u && hi > 0)) return false;
+  const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+  float y0f;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(((unsigned)fe << 23) | m23)));
+  const unsigned yb = __float_as_uint(y0f);
+  const int ey = (int)((yb >> 23) & 0xFF);
+  y0 = __hiloint2double(((ey + 896) << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
+  // y0 = my 2^(ey - 150) with my the 24-bit significand, so y0^2 = my^2 2^(2 ey - 300)
+  const unsigned long long my = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long p = my * my;                       // in [2^46, 2^48)
+  const int top = (int)(p >> 47);
+  const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
+  const long long e2 = 2 * (ey - 127) + top + 1023;
+  t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+  return true;
+}
+// 1/sqrt(r2), third-order correction of the seed (4 FP64 instructions)
+__device__ __forceinline__ double rsq_pair(double r2) {
+  double y0 = 0.0, t = 0.0;
+  if (rsqrt_seed_sq(r2, y0, t)) {
+    const double e = fma(-r2, t, 1.0);
+    return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+  }
+  return rsqrt(r2);
+}
+
+// per-level constants of the single-pair path, cached in shared memory
+enum {
+  LC_H, LC_HH, LC_T2, LC_R2, LC_A1, LC_B1, LC_A2, LC_B2, LC_GHA, LC_GHB, LC_T3, LC_MUNH, LC_H15,
+  LC_MUNHT2, LC_R2N, LC_R2P, LC_N
+};
+
+// Runs the sub-steps of levels >= k with F_{k-1} = {q}, from the opening of a sub-step at level
+// k.  X, V: this lane's component (packed layout).  Returns 0 when level k has finished (k is then
+// k - 1), 1 when the pair may be in contact at the next check (k is that check's level; the
+// general path takes the sub-step), 2 when the sub-step budget ran out.
+__device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, double *hs, int *cs,
+                                     double *lc, double &Xio, double &Vio, double gA, double gB,
+                                     double pR0sq, double piR0, double pRcut, int &kio, int &plev_io,
+                                     long long &substeps_io, int &deepest_io) {
+  const int pc = lane & 3, pb = (lane >> 2) & 1, cp = lane >> 3, base = lane & ~3;
+  const unsigned m0 = (cp & 1) ? 0xffffffffu : 0u, m1 = (cp & 2) ? 0xffffffffu : 0u;
+  const unsigned mb = pb ? 0xffffffffu : 0u;
+  const DiskDesc *dp = C.dp;
+  const double mu = C.mu;
+  const float muf = f32_trunc(mu);
+  double X = Xio, V = Vio;
+  long long substeps = substeps_io;
+  int deepest = deepest_io, plev = plev_io;
+  const int k0 = kio;
+  int j = k0, cj = cs[j];
+  unsigned long long have = 0ull;
+
+  // current level's constants
+  double h, hh, t2, R2, A1, B1, A2, B2, ghs, t3, munh, h15, munht2, R2n, R2p;
+  float hf;
+  auto set_level = [&](int jj) {
+    double *Lc = lc + LC_N * jj;
+    if (!((have >> jj) & 1ull)) {
+      const double hj = hs[jj];
+      // [h/2 | h^2 | R_j^2 | R_{j+1}^2]
+      const double s1 = fma4(m0, m1, hj, 0.5, -0.0, hj, hj, -0.0, pR0sq, dp->ck2[jj], -0.0,
+                             pR0sq, dp->ck2[jj + 1], -0.0);
+      const double hh_ = cpy(s1, lane, 0), t2_ = cpy(s1, lane, 1);
+      // weight argument (r - R_{j+1}) / (R_j - R_{j+1}) = r A1 + B1, and the same one level up
+      const double s2 = fma4(m0, m1, piR0, dp->invdc[jj], -0.0, dp->ck[jj + 1], dp->invdc[jj], -0.0,
+                             piR0, dp->invdc[jj - 1], -0.0, dp->ck[jj], dp->invdc[jj - 1], -0.0);
+      // [G m_a h/2 | G m_b h/2 | h^3 | -mu h]
+      const double s3 = fma4(m0, m1, gA, hh_, -0.0, gB, hh_, -0.0, t2_, hj, -0.0, mu, -hj, -0.0);
+      // [mu h/2 | 1.5 h | R_{j-1}^2]
+      const double s4 = fma4(m0, m1, mu, hh_, -0.0, hh_, 1.0, hj, pR0sq, dp->ck2[jj - 1], -0.0,
+                             mu, hh_, -0.0);
+      const double v[LC_N] = {hj, hh_, t2_, cpy(s1, lane, 2), cpy(s2, lane, 0), -cpy(s2, lane, 1),
+                              cpy(s2, lane, 2), -cpy(s2, lane, 3), cpy(s3, lane, 0),
+                              cpy(s3, lane, 1), cpy(s3, lane, 2), cpy(s3, lane, 3), cpy(s4, lane, 1),
+                              cpy(s4, lane, 0) * -hj, cpy(s1, lane, 3), cpy(s4, lane, 2)};
+#pragma unroll
+      for (int i = 0; i < LC_N; ++i) Lc[i] = v[i];
+      have |= 1ull << jj;
+    }
+    h = Lc[LC_H]; hh = Lc[LC_HH]; t2 = Lc[LC_T2]; R2 = Lc[LC_R2];
+    A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
+    ghs = pb ? -Lc[LC_GHA] : Lc[LC_GHB];
+    t3 = Lc[LC_T3]; munh = Lc[LC_MUNH]; h15 = Lc[LC_H15]; munht2 = Lc[LC_MUNHT2];
+    R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
+    hf = f32_trunc(h);
+  };
+
+  // separation x_b - x_a (this lane's component) and its square norm
+  double d = 0.0, r2 = 0.0;
+  auto sep = [&]() {
+    const double Xo = __shfl_xor_sync(FULL, X, 4);
+    d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
+    r2 = csum3(d * d, base);
+  };
+
+  // level-j force: hc = (h/2) w_j(r) G m_other / r^3 with this body's sign; fz when w_j = 0
+  double hc = 0.0;
+  bool fz = true;
+  auto forces = [&]() {
+    fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
+    if (fz) return;
+    const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
+    const double ri = rsq_pair(r2);
+    const double xw = fma(r2 * ri, inner ? A1 : A2, inner ? B1 : B2);
+    // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
+    const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
+    const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
+    const double ri2 = cpy(s1, lane, 3);
+    // [x^4 | x^2 qa + qb | 1/r^3]
+    const double s2 = fma4(m0, m1, x2, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2, x2, -0.0);
+    const double x4 = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
+    double w;
+    if (__double_as_longlong(xw) <= 0ll) {
+      w = inner ? 0.0 : 1.0;
+    } else if (!lt_nn(xw, 1.0)) {
+      w = inner ? 1.0 : 0.0;
+    } else {
+      w = inner ? x4 * q : fma(-x4, q, 1.0);
+    }
+    hc = w * (ri3 * ghs);
+  };
+
+  // (i): minimum distance of the straight-line relative motion over [0, h] below R_j
+  auto check = [&]() -> bool {
+    if (lt_nn(r2, R2)) return true;
+    const double Vo = __shfl_xor_sync(FULL, V, 4);
+    const double dv = bsel(V, Vo, mb) - bsel(Vo, V, mb);
+    const double vr = csum3(d * dv, base), v2 = csum3(dv * dv, base);
+    if (!is_neg(vr)) return false;
+    // [h v2 | vr^2 | R2 v2 | 2 vr]
+    const double s = fma4(m0, m1, h, v2, -0.0, vr, vr, -0.0, R2, v2, -0.0, vr, 2.0, -0.0);
+    const double hv2 = cpy(s, lane, 0);
+    if (lt_nn(neg(vr), hv2)) return lt_nn(fma(r2, v2, -cpy(s, lane, 1)), cpy(s, lane, 2));
+    const double e = fma(h, fma(h, v2, cpy(s, lane, 3)), r2);
+    return is_neg(e) || lt_nn(e, R2);
+  };
+
+  // Kepler drift of both bodies over h: Lagrange series of order 2 or 3 (common FP64 prefix,
+  // order chosen in FP32 meanwhile), else the scalar path
+  auto drift = [&]() {
+    // order of the series per body, from FP32 copies (the thresholds of drift_series)
+    const float xf = f32_trunc(X), vf = f32_trunc(V);
+    const float x0 = __shfl_sync(FULL, xf, base), x1 = __shfl_sync(FULL, xf, base + 1);
+    const float x2f = __shfl_sync(FULL, xf, base + 2);
+    const float v0 = __shfl_sync(FULL, vf, base), v1 = __shfl_sync(FULL, vf, base + 1);
+    const float v2f = __shfl_sync(FULL, vf, base + 2);
+    const float r2f = fmaf(x2f, x2f, fmaf(x1, x1, x0 * x0));
+    const float rvf = fmaf(x2f, v2f, fmaf(x1, v1, x0 * v0));
+    const float vvf = fmaf(v2f, v2f, fmaf(v1, v1, v0 * v0));
+    const float rif = rsqrtf(r2f), ri2f = rif * rif;
+    const float uf = muf * ri2f * rif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
+    const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
+    const unsigned ord =
+        __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
+    // FP64 prefix of both series
+    const double X1 = fma(h, V, X);
+    const double ri = rsq_pair(csum3(X * X, base));
+    if (ord == 2u) {
+      const double ri3 = ri * ri * ri;
+      const double fm1 = munht2 * ri3, fd = munh * ri3;      // f - 1 = -mu h^2/(2 r^3), f' = -mu h/r^3
+      const double Xn = fma(fm1, X, X1);
+      V = fma(fd, X, fma(fm1, V, V));
+      X = Xn;
+    } else if (ord == 3u) {
+      const double rv = csum3(X * V, base);
+      const double ri2 = ri * ri;
+      const double u = (mu * ri) * ri2, p = rv * ri2;
+      // [u p | -u/2 | -u/6]
+      const double s3 = fma4(m0, m1, u, p, -0.0, u, -0.5, -0.0, u, -1.0 / 6.0, -0.0, u, p, -0.0);
+      const double up = cpy(s3, lane, 0), nhu = cpy(s3, lane, 1), nu6 = cpy(s3, lane, 2);
+      // [h/2 up - u/2 | 1.5 h up - u | h up - u/2 | -u h^3/6]
+      const double s4 = fma4(m0, m1, hh, up, nhu, h15, up, -u, h, up, nhu, t3, nu6, -0.0);
+      // [f - 1 | f' | g' - 1 | x + h v + (g - h) v]
+      const double s5 = fma4(m0, m1, t2, cpy(s4, lane, 0), -0.0, h, cpy(s4, lane, 1), -0.0,
+                             t2, cpy(s4, lane, 2), -0.0, cpy(s4, lane, 3), V, X1);
+      const double fm1 = cpy(s5, lane, 0), fd = cpy(s5, lane, 1), gdm1 = cpy(s5, lane, 2);
+      const double Xn = fma(fm1, X, cpy(s5, lane, 3));
+      V = fma(fd, X, fma(gdm1, V, V));
+      X = Xn;
+    } else {
+      // longer intervals: the scalar series of order 6 or the Kepler solver, per body, in every
+      // lane of the body
+      double bx = SH(X, base), by = SH(X, base + 1), bz = SH(X, base + 2);
+      double bvx = SH(V, base), bvy = SH(V, base + 1), bvz = SH(V, base + 2);
+      if (!drift_series(mu, h, bx, by, bz, bvx, bvy, bvz)) {
+        const int st = kepler_drift(mu, h, bx, by, bz, bvx, bvy, bvz);
+        if (st != SYMBA_OK && pc == 0 && cp == 0) set_status(&D.stat[C.d], st);
+      }
+      __syncwarp();
+      X = pc == 0 ? bx : (pc == 1 ? by : (pc == 2 ? bz : 0.0));
+      V = pc == 0 ? bvx : (pc == 1 ? bvy : (pc == 2 ? bvz : 0.0));
+    }
+  };
+
+  int rc = 0;
+  int fat = -1;                 // level of the forces held in hc
+  bool start = true;
+  set_level(j);
+  sep();
+  for (;;) {
+    if (start) {
+      if (lt_nn(r2, pRcut)) { rc = 1; break; }
+      if (++substeps > C.max_substeps) { rc = 2; break; }
+      deepest = max(deepest, j);
+      const bool fl = check();
+      plev = fl ? j : j - 1;
+      if (fat != j) { forces(); fat = j; }
+      if (!fz) V = fma(hc, d, V);
+      const bool deeper = fl && (j + 1 <= C.max_depth);
+      if (fl && !deeper && lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
+      if (!deeper) {
+        drift();
+        sep();
+      } else {
+        cs[j] = cj;
+        ++j;
+        hs[j] = sub_interval(C, hs[j - 1]);
+        cj = 0;
+        set_level(j);
+        continue;
+      }
+      start = false;
+    }
+    forces();
+    fat = j;
+    if (!fz) V = fma(hc, d, V);
+    if (++cj < C.M) { start = true; continue; }
+    --j;
+    fat = -1;
+    if (j < k0) break;
+    cj = cs[j];
+    set_level(j);
+  }
+  if (j >= k0) cs[j] = cj;
+  kio = j;
+  Xio = X;
+  Vio = V;
+  substeps_io = substeps;
+  deepest_io = deepest;
+  plev_io = plev;
+  return rc;
+}
+
+__device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double *hs, int *cs, double *lc) {
   const int nm = C.mcnt, np = C.pcnt;
   const bool ism = lane < nm, isp = lane < np;
   // bodies
@@ -549,6 +857,39 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
   bool start = true, aborted = false;
   for (;;) {
     if (start) {
+      // a single pair below this level: the packed single-pair path
+      if (k >= 1 && C.l == 3) {
+        const unsigned Lm = __ballot_sync(FULL, isp && lev >= k - 1);
+        if (__popc(Lm) == 1) {
+          const int q = __ffs(Lm) - 1;
+          const int a_ = SH(ia, q), b_ = SH(ib, q);
+          if (SH(alive, a_) && SH(alive, b_)) {
+            const int pc = lane & 3, src = ((lane >> 2) & 1) ? b_ : a_;
+            const double px = SH(x, src), py = SH(y, src), pz = SH(z, src);
+            const double ux = SH(vx, src), uy = SH(vy, src), uz = SH(vz, src);
+            double X = pc == 0 ? px : (pc == 1 ? py : (pc == 2 ? pz : 0.0));
+            double V = pc == 0 ? ux : (pc == 1 ? uy : (pc == 2 ? uz : 0.0));
+            int plev = SH(lev, q);
+            const int rc = pair_run(D, C, lane, hs, cs, lc, X, V, SH(gm, a_), SH(gm, b_), SH(R0sq, q),
+                                    SH(iR0, q), SH(Rcut, q), k, plev, substeps, deepest);
+            const double ax_ = SH(X, 0), ay_ = SH(X, 1), az_ = SH(X, 2);
+            const double avx = SH(V, 0), avy = SH(V, 1), avz = SH(V, 2);
+            const double bx_ = SH(X, 4), by_ = SH(X, 5), bz_ = SH(X, 6);
+            const double bvx = SH(V, 4), bvy = SH(V, 5), bvz = SH(V, 6);
+            if (lane == a_) { x = ax_; y = ay_; z = az_; vx = avx; vy = avy; vz = avz; }
+            if (lane == b_) { x = bx_; y = by_; z = bz_; vx = bvx; vy = bvy; vz = bvz; }
+            if (lane == q) lev = plev;
+            forces_at = -1;
+            if (rc == 0) {            // level k + 1 finished: continue with the closing kick of k
+              if (k == 0) break;
+              start = false;
+              continue;
+            }
+            if (rc == 2) { aborted = true; break; }
+            // rc == 1: a contact may be due; this sub-step takes the general path
+          }
+        }
+      }
       ++substeps;
       if (substeps > C.max_substeps) { aborted = true; break; }
       deepest = max(deepest, k);
@@ -561,7 +902,7 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
       drift(k, hs[k], fk && !deeper);
       if (deeper) {
         ++k;
-        hs[k] = hs[k - 1] / (double)C.M;
+        hs[k] = sub_interval(C, hs[k - 1]);
         cs[k] = 0;
         continue;
       }
@@ -579,6 +920,7 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
   if (lane == 0) {
     atomicMax(&D.stat[C.d].max_depth, deepest);
     atomicAdd(&D.stat[C.d].substeps, (unsigned long long)substeps);
+    atomicMax(&D.stat[C.d].max_chain, (unsigned long long)substeps);
   }
   if (ism) {
     D.x[pglob] = x; D.y[pglob] = y; D.z[pglob] = z;
@@ -600,9 +942,12 @@ __device__ void run_group(const Dev &D, int g, int lane, const Levels &V, SmallV
   C.M = C.dp->M; C.l = C.dp->l; C.max_depth = C.dp->max_depth; C.max_substeps = C.dp->max_substeps;
   C.dt = C.dp->dt; C.lam = C.dp->hill_scale; C.G = C.dp->G;
   C.mu = __dmul_rn(C.dp->G, C.dp->m0);
+  C.invM = 1.0 / (double)C.M;
 
   if (C.mcnt <= 32 && C.pcnt <= 32) {
-    run_group_regs(D, C, lane, V.h, V.cnt);
+    static_assert(sizeof(SmallView) >= sizeof(double) * LC_N * (SYM_MAX_LEVELS + 2),
+                  "level-constant cache of the single-pair path");
+    run_group_regs(D, C, lane, V.h, V.cnt, reinterpret_cast<double *>(sv));
     return;
   }
   GView S;

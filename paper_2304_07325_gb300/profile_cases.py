@@ -35,11 +35,13 @@ def main(argv=None):
     ph = s.profile_step(a.steps)
     st = s.stats()
     status = s.sync()
-    print(f"case {a.case} status {status} substeps {st.substeps} depth {st.max_depth}")
+    print(f"case {a.case} status {status} substeps {st.substeps} depth {st.max_depth} "
+          f"longest chain {st.max_chain}")
     for name, ms in zip(PHASES, ph):
         print(f"  {name:28s} {ms:10.3f} ms")
     if st.substeps:
         print(f"  recursion per sub-step      {1e3 * ph[5] / st.substeps:10.3f} us")
+        print(f"  per longest-chain sub-step  {1e3 * ph[5] / st.max_chain:10.3f} us")
     s.close()
     return 0 if status >= 0 else 1
 

@@ -40,7 +40,7 @@ def test_param_struct_layout_matches_header(built_lib):
     assert (p.dt, p.M, p.shell_ratio, p.l, p.hill_scale, p.max_depth) == (0.5, 4, 2.08, 3, 6.5, 20)
     assert abs(p.G - 39.47841760435743) < 1e-14 and p.m0 == 1.0 and p.precision == 0
     assert ctypes.sizeof(sy.symba_params) == 5 * 8 + 6 * 4
-    assert ctypes.sizeof(sy.symba_stats) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(sy.symba_stats) == 4 * 4 + 4 * 8
 
 
 def test_status_strings(built_lib):
