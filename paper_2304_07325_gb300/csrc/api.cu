@@ -347,6 +347,7 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   A(&D.acc, 3 * n);
   A(&D.g_moff, gs); A(&D.g_mcnt, gs); A(&D.g_poff, gs); A(&D.g_pcnt, gs); A(&D.g_cur, gs);
   A(&D.gmem, n); A(&D.rec_items, gs); A(&D.rec_total, 1);
+  A(&D.lcache, (size_t)P->L.rec_blocks * 4 * SYM_PAIR_LC);
   A(&P->eacc, 4 * (SA_NDIG + 1)); A(&P->eout, 4);
   if (st != SYMBA_OK) { symba_pool_free(P); return st; }
   if (cudaMemsetAsync(D.blk_disk, 0xFF, sizeof(int) * (n / SYM_TILE + 1), P->stream) != cudaSuccess ||

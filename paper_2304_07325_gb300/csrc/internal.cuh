@@ -15,6 +15,7 @@
 
 #define SYM_TILE 32
 #define SYM_MAX_LEVELS 32
+#define SYM_PAIR_LC (16 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
 #define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
 
 struct DiskDesc {
@@ -77,6 +78,7 @@ struct Dev {
   int *gmem;                    // members grouped by group (global particle indices)
   int *rec_items;               // recursion work list (global group slot)
   int *rec_total;               // number of items
+  double *lcache;               // [recursion warp][SYM_PAIR_LC] single-pair level constants
 };
 
 // --------------------------------------------------------------------------------------------

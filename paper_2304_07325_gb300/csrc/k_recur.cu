@@ -297,7 +297,12 @@ __device__ void drift_range(const GView &S, const GroupCtx &C, const Dev &D, int
   __syncwarp();
 }
 
-__device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const Levels &V, int lane) {
+__device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, double *hs, int *cs,
+                                     double *lc, double &Xio, double &Vio, double gA, double gB,
+                                     double pR0sq, double piR0, double pRcut, int &kio, int &plev_io,
+                                     long long &substeps_io, int &deepest_io);
+
+__device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const Levels &V, int lane, double *lc) {
   int k = 1, deepest = 1, forces_at = -1;
   long long substeps = 0;
   V.h[1] = C.dt / (double)C.M;
@@ -307,6 +312,39 @@ __device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const L
   bool start = true, aborted = false;
   for (;;) {
     if (start) {
+      // a single pair below this level: the packed single-pair path
+      if (k >= 1 && C.l == 3 && V.lenL[k] == 1) {
+        const int q = S.perm[0];
+        const int a = S.pa[q], b = S.pb[q];
+        if (S.alive[a] && S.alive[b]) {
+          const int pc = lane & 3, src = ((lane >> 2) & 1) ? b : a;
+          double X = pc == 0 ? S.x[src] : (pc == 1 ? S.y[src] : (pc == 2 ? S.z[src] : 0.0));
+          double Vv = pc == 0 ? S.vx[src] : (pc == 1 ? S.vy[src] : (pc == 2 ? S.vz[src] : 0.0));
+          const double R0 = S.R0[q], Rc = S.rad[a] + S.rad[b];
+          int plev = S.lev[q];
+          const int k0 = k;
+          __syncwarp();
+          const int rc = pair_run(D, C, lane, V.h, V.cnt, lc, X, Vv, S.gm[a], S.gm[b], R0 * R0,
+                                  S.invR0[q], 1.0000001 * (Rc * Rc), k, plev, substeps, deepest);
+          if (lane < 8 && pc < 3) {
+            double *px = pc == 0 ? S.x : (pc == 1 ? S.y : S.z);
+            double *pv = pc == 0 ? S.vx : (pc == 1 ? S.vy : S.vz);
+            px[src] = X;
+            pv[src] = Vv;
+          }
+          if (lane == 0) S.lev[q] = plev;
+          // levels entered below k0 hold the same single pair and its two bodies
+          for (int i = k0 + 1 + lane; i <= k; i += 32) { V.lenL[i] = 1; V.lenM[i] = V.lenM[k0]; }
+          __syncwarp();
+          forces_at = -1;
+          if (rc == 0) {
+            if (k == 0) break;
+            start = false;
+            continue;
+          }
+          if (rc == 2) { aborted = true; break; }
+        }
+      }
       ++substeps;
       if (substeps > C.max_substeps) { aborted = true; break; }
       deepest = max(deepest, k);
@@ -931,7 +969,7 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
   __syncwarp();
 }
 
-__device__ void run_group(const Dev &D, int g, int lane, const Levels &V, SmallView *sv) {
+__device__ void run_group(const Dev &D, int g, int lane, const Levels &V, SmallView *sv, double *lc) {
   GroupCtx C;
   C.moff = D.g_moff[g];
   C.mcnt = D.g_mcnt[g];
@@ -945,9 +983,7 @@ __device__ void run_group(const Dev &D, int g, int lane, const Levels &V, SmallV
   C.invM = 1.0 / (double)C.M;
 
   if (C.mcnt <= 32 && C.pcnt <= 32) {
-    static_assert(sizeof(SmallView) >= sizeof(double) * LC_N * (SYM_MAX_LEVELS + 2),
-                  "level-constant cache of the single-pair path");
-    run_group_regs(D, C, lane, V.h, V.cnt, reinterpret_cast<double *>(sv));
+    run_group_regs(D, C, lane, V.h, V.cnt, lc);
     return;
   }
   GView S;
@@ -1000,7 +1036,7 @@ __device__ void run_group(const Dev &D, int g, int lane, const Levels &V, SmallV
   }
   __syncwarp();
 
-  recurse(S, C, D, V, lane);
+  recurse(S, C, D, V, lane, lc);
 
   // scatter back
   for (int a = lane; a < C.mcnt; a += 32) {
@@ -1019,13 +1055,14 @@ __global__ void __launch_bounds__(128) k_recursion(Dev D) {
   __shared__ SmallView sview[4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Levels V{hs[w], cs[w], ls[w], ms[w]};
+  double *lc = D.lcache + (size_t)(blockIdx.x * 4 + w) * SYM_PAIR_LC;
   const int total = *D.rec_total;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&D.work[2], 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= total) break;
-    run_group(D, D.rec_items[item], lane, V, &sview[w]);
+    run_group(D, D.rec_items[item], lane, V, &sview[w], lc);
   }
 }
 
