@@ -534,7 +534,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // current level's constants
   double h, hh, t2, R2, A1, B1, A2, B2, ghs, t3, munh, h15, munht2, R2n, R2p;
-  float hf;
+  float hf, R2f;
   auto set_level = [&](int jj) {
     double *Lc = lc + LC_N * jj;
     if (!((have >> jj) & 1ull)) {
@@ -565,48 +565,74 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     t3 = Lc[LC_T3]; munh = Lc[LC_MUNH]; h15 = Lc[LC_H15]; munht2 = Lc[LC_MUNHT2];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
     hf = f32_trunc(h);
+    R2f = f32_trunc(R2) * (1.0f + 3.0517578e-5f);     // not below R2
   };
 
-  // separation x_b - x_a (this lane's component) and its square norm
+  // separation x_b - x_a (this lane's component), its square norm, and that in FP32 (not above)
   double d = 0.0, r2 = 0.0;
+  float r2f = 0.0f;
   auto sep = [&]() {
     const double Xo = __shfl_xor_sync(FULL, X, 4);
     d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
     r2 = csum3(d * d, base);
+    r2f = f32_trunc(r2);
   };
 
-  // level-j force: hc = (h/2) w_j(r) G m_other / r^3 with this body's sign; fz when w_j = 0
+  // level-j force: hc = (h/2) w_j(r) G m_other / r^3 with this body's sign, zero when w_j
+  // vanishes (fz: outside [R_{j+1}, R_{j-1})).  Branch-free, so that it schedules together with
+  // the work around it; forces_skip() leaves it out when the weight vanishes.
   double hc = 0.0;
   bool fz = true;
   auto forces = [&]() {
     fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
-    if (fz) return;
     const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
+    const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
+    const double g = fz ? 0.0 : ghs;
     const double ri = rsq_pair(r2);
-    const double xw = fma(r2 * ri, inner ? A1 : A2, inner ? B1 : B2);
+    const double xw = fma(r2 * ri, A, B);
     // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
     const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
-    // [x^4 | x^2 qa + qb | 1/r^3]
-    const double s2 = fma4(m0, m1, x2, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2, x2, -0.0);
-    const double x4 = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
-    double w;
-    if (__double_as_longlong(xw) <= 0ll) {
-      w = inner ? 0.0 : 1.0;
-    } else if (!lt_nn(xw, 1.0)) {
-      w = inner ? 1.0 : 0.0;
-    } else {
-      w = inner ? x4 * q : fma(-x4, q, 1.0);
-    }
-    hc = w * (ri3 * ghs);
+    // [+-x^4 | x^2 qa + qb | 1/r^3]  (the sign of x^4 picks f or 1 - f)
+    const double x2s = inner ? x2 : neg(x2);
+    const double s2 = fma4(m0, m1, x2s, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2s, x2, -0.0);
+    const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
+    // no clamp of x to [0, 1]: outside [R_{j+1}, R_{j-1}) the weight is zero (fz, x = 0 above),
+    // inside x leaves [0, 1] only by rounding, where f_3 (flat at both ends) differs from 0 or
+    // 1 by O(x^4) or O((x - 1)^2)
+    const double w = fma(x4s, q, inner ? -0.0 : 1.0);
+    hc = w * (ri3 * g);
+  };
+  auto forces_skip = [&]() {
+    fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
+    if (fz) { hc = 0.0; return; }
+    forces();
   };
 
-  // (i): minimum distance of the straight-line relative motion over [0, h] below R_j
-  auto check = [&]() -> bool {
+  // (i): minimum distance of the straight-line relative motion over [0, h] below R_j, for the
+  // velocities U (before this sub-step's opening kick).  far_apart() is a conservative FP32 test
+  // of the common case, |d| - |dv| h > R_j, with relative margins of 2^-15, far above the
+  // rounding of its FP32 copies (truncation 2^-23 per operand), so it never clears a pair the
+  // FP64 predicate would flag; check_exact() is the FP64 predicate.
+  auto far_apart = [&](double U) -> bool {
+    const float uf = f32_trunc(U), uo = __shfl_xor_sync(FULL, uf, 4);
+    const float dvf = pb ? uf - uo : uo - uf, av = fabsf(uf) + fabsf(uo);
+    const float p0 = dvf * dvf;
+    const float s2 = (__shfl_sync(FULL, p0, base) + __shfl_sync(FULL, p0, base + 1)) +
+                     __shfl_sync(FULL, p0, base + 2);
+    const float sa = (__shfl_sync(FULL, av, base) + __shfl_sync(FULL, av, base + 1)) +
+                     __shfl_sync(FULL, av, base + 2);
+    const float m = 1.0f + 3.0517578e-5f;                       // 1 + 2^-15
+    const float dvmag = sqrtf(s2) * m + sa * 2.3841858e-7f;      // |dv| + truncation error (2^-22)
+    const float dlo = sqrtf(r2f) * (1.0f - 3.0517578e-5f);
+    const float rhs = (sqrtf(R2f) + dvmag * hf * m) * m;
+    return R2f > 0.0f && dlo > rhs;                             // NaN and underflow: false
+  };
+  auto check_exact = [&](double U) -> bool {
     if (lt_nn(r2, R2)) return true;
-    const double Vo = __shfl_xor_sync(FULL, V, 4);
-    const double dv = bsel(V, Vo, mb) - bsel(Vo, V, mb);
+    const double Uo = __shfl_xor_sync(FULL, U, 4);
+    const double dv = bsel(U, Uo, mb) - bsel(Uo, U, mb);
     const double vr = csum3(d * dv, base), v2 = csum3(dv * dv, base);
     if (!is_neg(vr)) return false;
     // [h v2 | vr^2 | R2 v2 | 2 vr]
@@ -617,36 +643,45 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     return is_neg(e) || lt_nn(e, R2);
   };
 
-  // Kepler drift of both bodies over h: Lagrange series of order 2 or 3 (common FP64 prefix,
-  // order chosen in FP32 meanwhile), else the scalar path
-  auto drift = [&]() {
-    // order of the series per body, from FP32 copies (the thresholds of drift_series)
+  // distance of this lane's body from the sun at the current positions: 1/r, 1/r^2, 1/r^3 and
+  // r^2 in FP32, computed right after every drift so that it overlaps the pair's force chain
+  double rbi = 0.0, rb2 = 0.0, rb3 = 0.0;
+  float rbf2 = 0.0f;
+  auto body_r = [&]() {
+    const double rr = csum3(X * X, base);
+    rbf2 = f32_trunc(rr);
+    rbi = rsq_pair(rr);
+    rb2 = rbi * rbi;
+    rb3 = rb2 * rbi;
+  };
+
+  // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
+  // drift_series): 2, 3, 6, or 9 for the Kepler solver
+  auto drift_order = [&]() -> unsigned {
     const float xf = f32_trunc(X), vf = f32_trunc(V);
     const float x0 = __shfl_sync(FULL, xf, base), x1 = __shfl_sync(FULL, xf, base + 1);
     const float x2f = __shfl_sync(FULL, xf, base + 2);
     const float v0 = __shfl_sync(FULL, vf, base), v1 = __shfl_sync(FULL, vf, base + 1);
     const float v2f = __shfl_sync(FULL, vf, base + 2);
-    const float r2f = fmaf(x2f, x2f, fmaf(x1, x1, x0 * x0));
     const float rvf = fmaf(x2f, v2f, fmaf(x1, v1, x0 * v0));
     const float vvf = fmaf(v2f, v2f, fmaf(v1, v1, v0 * v0));
-    const float rif = rsqrtf(r2f), ri2f = rif * rif;
+    const float rif = rsqrtf(rbf2), ri2f = rif * rif;
     const float uf = muf * ri2f * rif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
-    const unsigned ord =
-        __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
-    // FP64 prefix of both series
+    return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
+  };
+
+  // Kepler drift of both bodies over h: Lagrange series of order 2 or 3, else the scalar path
+  auto drift = [&](unsigned ord) {
     const double X1 = fma(h, V, X);
-    const double ri = rsq_pair(csum3(X * X, base));
     if (ord == 2u) {
-      const double ri3 = ri * ri * ri;
-      const double fm1 = munht2 * ri3, fd = munh * ri3;      // f - 1 = -mu h^2/(2 r^3), f' = -mu h/r^3
+      const double fm1 = munht2 * rb3, fd = munh * rb3;      // f - 1 = -mu h^2/(2 r^3), f' = -mu h/r^3
       const double Xn = fma(fm1, X, X1);
       V = fma(fd, X, fma(fm1, V, V));
       X = Xn;
     } else if (ord == 3u) {
       const double rv = csum3(X * V, base);
-      const double ri2 = ri * ri;
-      const double u = (mu * ri) * ri2, p = rv * ri2;
+      const double u = mu * rb3, p = rv * rb2;
       // [u p | -u/2 | -u/6]
       const double s3 = fma4(m0, m1, u, p, -0.0, u, -0.5, -0.0, u, -1.0 / 6.0, -0.0, u, p, -0.0);
       const double up = cpy(s3, lane, 0), nhu = cpy(s3, lane, 1), nu6 = cpy(s3, lane, 2);
@@ -679,36 +714,63 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   bool start = true;
   set_level(j);
   sep();
+  body_r();
   for (;;) {
+    bool level_done = false;
     if (start) {
       if (lt_nn(r2, pRcut)) { rc = 1; break; }
       if (++substeps > C.max_substeps) { rc = 2; break; }
       deepest = max(deepest, j);
-      const bool fl = check();
-      plev = fl ? j : j - 1;
-      if (fat != j) { forces(); fat = j; }
-      if (!fz) V = fma(hc, d, V);
-      const bool deeper = fl && (j + 1 <= C.max_depth);
-      if (fl && !deeper && lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
-      if (!deeper) {
-        drift();
+      if (fat != j) { forces_skip(); fat = j; }
+      const double U = V;                  // velocities the check sees
+      V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
+      const bool far = far_apart(U);
+      const unsigned ord = drift_order();
+      if (far && ord == 2u) {
+        // the common sub-step as one straight block: F_j stays empty, series of order 2,
+        // closing force and kick, and the next distances from the sun
+        plev = j - 1;
+        const double X1 = fma(h, V, X);
+        const double fm1 = munht2 * rb3, fd = munh * rb3;
+        const double Xn = fma(fm1, X, X1);
+        V = fma(fd, X, fma(fm1, V, V));
+        X = Xn;
         sep();
+        forces();
+        V = fma(hc, d, V);
+        body_r();
+        fat = j;
+        if (++cj < C.M) continue;
+        level_done = true;
       } else {
-        cs[j] = cj;
-        ++j;
-        hs[j] = sub_interval(C, hs[j - 1]);
-        cj = 0;
-        set_level(j);
-        continue;
+        const bool fl = !far && check_exact(U);
+        plev = fl ? j : j - 1;
+        const bool deeper = fl && (j + 1 <= C.max_depth);
+        if (fl && !deeper && lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
+        if (!deeper) {
+          drift(ord);
+          sep();
+          body_r();
+        } else {
+          cs[j] = cj;
+          ++j;
+          hs[j] = sub_interval(C, hs[j - 1]);
+          cj = 0;
+          set_level(j);
+          continue;
+        }
+        start = false;
       }
-      start = false;
     }
-    forces();
-    fat = j;
-    if (!fz) V = fma(hc, d, V);
-    if (++cj < C.M) { start = true; continue; }
+    if (!level_done) {
+      forces_skip();
+      fat = j;
+      V = fma(hc, d, V);
+      if (++cj < C.M) { start = true; continue; }
+    }
     --j;
     fat = -1;
+    start = false;
     if (j < k0) break;
     cj = cs[j];
     set_level(j);
