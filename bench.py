@@ -30,9 +30,13 @@ import numpy as np  # noqa: E402
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (no tensor cores for this path)
 FLOPS_PER_PAIR_KICK = 26          # 3 sub, 5 r^2, 2 for 1/sqrt, 2 for r^-3, 2 mass scalings, 12 FMA flops
 FLOPS_PER_PAIR_CHECK = 18
-# one recursion sub-step of the dominant case (a bound pair: 1 pair, 2 bodies): the check (18),
-# two kicks (2 x 26) and two Kepler drifts (2 x 50)
-FLOPS_PER_SUBSTEP = 18 + 2 * 26 + 2 * 50
+# The group recursion is a chain of dependent sub-steps per group; the longest chain sets the step
+# time.  Its roofline is the FP64 latency of one warp: a GB300 warp completes one FP64 instruction
+# per DFMA_LATENCY_CYCLES (dependent or not; measured with a dependent DFMA chain), and a chain
+# sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
+# (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
+DFMA_LATENCY_CYCLES = 64.3
+FP64_INSTR_PER_CHAIN_SUBSTEP = 37.5
 # the trapezoid kick kernel at N = 10,000, one ncu capture (kick 1): DRAM read + write per launch
 KICK_TRAFFIC_BYTES_N10000 = (1.829120 + 14.927104) * 1e6
 
@@ -51,9 +55,10 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve", "field"],
                     help="single: the N=10k headline; batched: 64 disks in one pool vs one at a time; "
-                         "serve: Poisson request stream through the continuous-batching server")
+                         "serve: Poisson request stream through the continuous-batching server; "
+                         "field: N_m massive + field particles, mixed vs FP64 (use --n 1000)")
     ap.add_argument("--systems", type=int, default=64)
     ap.add_argument("--n-lo", type=int, default=1000)
     ap.add_argument("--n-hi", type=int, default=10000)
@@ -233,7 +238,7 @@ def run_ours(args):
     clocks.start()
     t_wall0 = time.perf_counter()
     depth_max, substeps = 0, 0
-    chain_us = []                              # recursion time per sub-step of the longest chain
+    chain_us_list = []                         # recursion time per sub-step of the longest chain
     chain_max = 0
     for k in range(args.steps):
         if flush is not None:
@@ -247,7 +252,7 @@ def run_ours(args):
         substeps += s.substeps
         chain_max = max(chain_max, s.max_chain)
         if s.max_chain > 0:
-            chain_us.append(1e3 * ph[5] / s.max_chain)
+            chain_us_list.append(1e3 * ph[5] / s.max_chain)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -285,15 +290,25 @@ def run_ours(args):
         kick_flops = FLOPS_PER_PAIR_KICK * P
         kick_achieved = kick_flops / (kick_ms * 1e-3) / 1e12
         rec_ms = phase_tot[5] / args.steps
-        rec_achieved = FLOPS_PER_SUBSTEP * (substeps / args.steps) / max(rec_ms * 1e-3, 1e-12) / 1e12
         peak_note = "GB300 FP64 1.25 TFLOP/s (recipe's figure; a DFMA loop measured 1.19 here)"
-        # the dominant kernel by time: the group recursion, a chain of dependent sub-steps per group
+        # the dominant kernel by time: the group recursion, bound by the FP64 latency of the warp
+        # that runs the longest chain of dependent sub-steps
+        sm_hz = 1e6 * (clk.get("sm_mhz") or 2070.0)
+        chain_peak = sm_hz / DFMA_LATENCY_CYCLES / 1e6                    # M FP64 instr/s, one warp
+        chain_us = statistics.median(chain_us_list) if chain_us_list else float("nan")
+        chain_achieved = FP64_INSTR_PER_CHAIN_SUBSTEP / chain_us         # M FP64 instr/s
         roofline = {"kernel": "k_recursion (per-group recursive sub-stepping)", "bound": "alu",
-                    "achieved": rec_achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                    "frac": rec_achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
-                    "share_of_step": phase_tot[5] / phase_tot.sum(), "peak_source": peak_note,
-                    "note": "latency-bound: each group's sub-steps form one dependent chain on one SM "
-                            "quadrant's FP64 pipe; the longest chain sets the step time"}
+                    "achieved": chain_achieved, "peak": chain_peak,
+                    "unit": "M FP64 warp-instr/s on the longest group chain (one warp)",
+                    "frac": chain_achieved / chain_peak, "traffic": None,
+                    "share_of_step": phase_tot[5] / phase_tot.sum(),
+                    "peak_source": f"SM clock {sm_hz / 1e6:.0f} MHz / {DFMA_LATENCY_CYCLES} cycles per "
+                                   "dependent FP64 instruction (measured)",
+                    "fp64_instr_per_chain_substep": FP64_INSTR_PER_CHAIN_SUBSTEP,
+                    "us_per_chain_substep": chain_us,
+                    "note": "latency-bound: one warp runs a group's dependent sub-steps; the longest "
+                            "chain sets the step time; the rest of each sub-step is shuffles, branches "
+                            "and issue"}
         roofline_kick = {"kernel": "k_trap_fp64 (trapezoid pair kick)", "bound": "alu", "achieved": kick_achieved,
                          "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                          "frac": kick_achieved / FP64_PEAK_TFLOPS_NOMINAL,
@@ -317,7 +332,7 @@ def run_ours(args):
                 "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "phase_ms_per_step": phases, "max_depth": depth_max,
                 "substeps_per_step": substeps / args.steps, "longest_chain_substeps": chain_max,
-                "us_per_chain_substep_median": statistics.median(chain_us) if chain_us else None,
+                "us_per_chain_substep_median": statistics.median(chain_us_list) if chain_us_list else None,
                 "roofline": roofline, "roofline_kick": roofline_kick, "cpu_baseline": cb,
                 "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
                         "h2d_bytes_per_step": 2 * 8 * 3 * ntot, "d2h_bytes_per_step": 2 * 8 * 3 * ntot,
@@ -420,6 +435,63 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_field(args):
+    """Field-particle-dominated disk (N_m massive + n_field massless; default 1,000 + 100,000):
+    the mixed-precision path (FP32 pair math, FP64 state) timed per step, and its accuracy after
+    the same number of steps against the FP64 path from the same input (energy error of each,
+    largest relative position difference).  Metric: pair interactions per second."""
+    import torch
+
+    import paper_2304_07325_gb300 as sy
+    from paper_2304_07325_gb300 import build, disk
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nm, nf = args.n, args.n_field if args.n_field > 0 else 100000
+    d = disk.planetesimal_disk(nm, 1003, n_field=nf)
+    P = nm * (nm - 1) // 2 + nm * nf
+    out = {}
+    for name, prec in (("mixed", sy.SYMBA_PRECISION_MIXED), ("fp64", sy.SYMBA_PRECISION_FP64)):
+        s = sy.System(d.x, d.v, d.m, d.radius, n_massive=nm, params=sy.default_params(precision=prec))
+        E0, _ = s.energy()
+        s.profile_step(max(1, args.warmup))
+        clocks = ClockSampler(0)
+        torch.cuda.synchronize()
+        clocks.start()
+        ph = np.zeros(sy.SYMBA_NPHASES)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ph += s.profile_step(1)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        st = s.sync()
+        if st < 0:
+            raise RuntimeError(f"{name}: {sy.status_string(st)}")
+        E1, _ = s.energy()
+        x, *_ = s.get_state()
+        dev_ms = float(ph.sum())
+        out[name] = {"ms_per_step": dev_ms / args.steps, "pairs_per_s": 2.0 * P * args.steps / (dev_ms * 1e-3),
+                     "dE_rel": abs((E1 - E0) / E0), "x": x, "clocks": clk, "wall_s": wall,
+                     "kick_ms": float(ph[1] + ph[6]) / (2 * args.steps)}
+        s.close()
+    xm, xd = out["mixed"].pop("x"), out["fp64"].pop("x")
+    rel = np.linalg.norm(xm - xd, axis=1) / np.linalg.norm(xd, axis=1)
+    dx = {"p50": float(np.percentile(rel, 50)), "p99": float(np.percentile(rel, 99)),
+          "max": float(rel.max()), "frac_below_1e-10": float(np.mean(rel < 1e-10)),
+          "note": "close encounters amplify rounding differences; the tail is chaotic divergence"}
+    m = out["mixed"]
+    line = {"metric": "pair-interactions/s", "value": m["pairs_per_s"], "unit": "pair-interactions/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-pair/f64-state", "data": "synthetic",
+            "config": {"workload": f"field-dominated disk N_m={nm} + {nf} massless (seed 1003), dt=0.5 yr, "
+                                   "M=4, R_k/R_k+1=2.08, l=3", "pairs_per_kick": P, "l2": "inputs > L2"},
+            "mixed": m, "fp64": out["fp64"],
+            "rel_dx_mixed_vs_fp64": dx, "clocks": m["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -428,6 +500,8 @@ def main():
         run_batched(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "field":
+        run_field(args)
     else:
         run_ours(args)
 

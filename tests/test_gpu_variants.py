@@ -1,0 +1,77 @@
+"""Parameter variants of the method against the oracle (needs a GB300): the original-SyMBA
+setting M = 3 with the l = 1 changeover, other subdivision factors, shell ratios and changeover
+orders (Sec. 3 names M, R_k/R_{k+1} and l as the method's parameters).  The single-pair path is
+specific to l = 3, so l != 3 runs the general recursion throughout.
+
+Bars as for the benchmark parameters: level-0 encounter pairs and groups bit-exact; positions to
+1e-12 relative or within 100x the oracle's rounding-level sensitivity twin, each step started
+from the oracle's state."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from paper_2304_07325_gb300 import disk  # noqa: E402
+
+VARIANTS = [
+    dict(M=3, l=1, shell_ratio=2.08),
+    dict(M=3, l=3, shell_ratio=2.08),
+    dict(M=2, l=2, shell_ratio=1.6),
+    dict(M=5, l=3, shell_ratio=2.9),
+    dict(M=4, l=4, shell_ratio=2.08),
+]
+
+
+@pytest.fixture(scope="module")
+def sy():
+    import paper_2304_07325_gb300 as m
+    from paper_2304_07325_gb300 import build
+    build.build()
+    return m
+
+
+@pytest.mark.parametrize("var", VARIANTS, ids=lambda v: f"M{v['M']}_l{v['l']}_r{v['shell_ratio']}")
+def test_variant_steps_from_oracle_states(orc, sy, var):
+    d = disk.planetesimal_disk(1000, 1000)
+    ref = orc.OracleSim(d.x, d.v, d.m, d.radius, params=orc.make_params(**var))
+    gpu = sy.System(d.x, d.v, d.m, d.radius, rhill=ref.rhill, params=sy.default_params(**var))
+    deepest = 0
+    for _ in range(8):
+        twin = orc.OracleSim(d.x, d.v, d.m, d.radius, rhill=ref.rhill,
+                             params=orc.make_params(noise=1, **var))
+        twin.set_state(ref.x, ref.v)
+        twin.alive[...] = ref.alive
+        twin.m[...] = ref.m
+        twin.radius[...] = ref.radius
+        twin.rhill[...] = ref.rhill
+        gpu.set_state(ref.x, ref.v)
+        assert ref.step(1) >= 0 and twin.step(1) >= 0
+        gpu.step(1)
+        assert gpu.sync() >= 0
+        p_ref, g_ref, ng_ref = ref.enc_groups()
+        p_gpu, g_gpu, ng_gpu = gpu.enc_groups()
+        assert ng_ref == ng_gpu and np.array_equal(p_ref, p_gpu) and np.array_equal(g_ref, g_gpu)
+        x, v, m, r, a = gpu.get_state()
+        assert np.array_equal(a, ref.alive)
+        norm = np.linalg.norm(ref.x, axis=1)
+        rel = np.linalg.norm(x - ref.x, axis=1) / norm
+        spread = np.linalg.norm(twin.x - ref.x, axis=1) / norm
+        bad = np.where(rel > np.maximum(1e-12, 100.0 * spread))[0]
+        assert len(bad) == 0, [(int(i), rel[i], spread[i]) for i in bad[:5]]
+        deepest = max(deepest, gpu.stats().max_depth)
+    assert deepest >= 2
+
+
+def test_variant_energy_conservation(sy):
+    """l = 1 and M = 3 on the 100-body accuracy disk: energy error bounded like l = 3's."""
+    d = disk.hill_spaced_disk()
+    out = {}
+    for var in (dict(M=3, l=1, shell_ratio=2.08), dict(M=4, l=3, shell_ratio=2.08)):
+        s = sy.System(d.x, d.v, d.m, d.radius, params=sy.default_params(dt=0.1, **var))
+        E0, _ = s.energy()
+        s.step(1000)
+        assert s.sync() >= 0
+        E1, _ = s.energy()
+        out[var["l"]] = abs((E1 - E0) / E0)
+        s.close()
+    assert out[1] < 1e-9 and out[3] < 1e-9
