@@ -495,6 +495,30 @@ __device__ __forceinline__ bool rsqrt_seed_sq(double r2, double &y0, double &t) 
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
   return true;
 }
+// The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
+// FP64 sum that forms r2: the seed's square t stays exact, so the third-order correction from
+// e = 1 - r2 t still reaches full FP64 accuracy.  Every lane of the warp must call it.
+__device__ __forceinline__ double rsq_est(double r2, float r2e) {
+  const unsigned yb = __float_as_uint(r2e);
+  const int fe = (int)((yb >> 23) & 0xFF);
+  if (__all_sync(FULL, fe >= 1 && fe <= 253 && (int)yb > 0)) {
+    float y0f;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2e));
+    const unsigned b = __float_as_uint(y0f);
+    const int ey = (int)((b >> 23) & 0xFF);
+    const double y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
+    const unsigned long long my = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const unsigned long long p = my * my;
+    const int top = (int)(p >> 47);
+    const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
+    const long long e2 = 2 * (ey - 127) + top + 1023;
+    const double t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+    const double e = fma(-r2, t, 1.0);
+    return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+  }
+  return rsqrt(r2);
+}
+
 // 1/sqrt(r2), third-order correction of the seed (4 FP64 instructions)
 __device__ __forceinline__ double rsq_pair(double r2) {
   double y0 = 0.0, t = 0.0;
@@ -570,10 +594,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // separation x_b - x_a (this lane's component), its square norm, and that in FP32 (not above)
   double d = 0.0, r2 = 0.0;
-  float r2f = 0.0f;
+  float r2f = 0.0f, r2e = 0.0f;
   auto sep = [&]() {
     const double Xo = __shfl_xor_sync(FULL, X, 4);
     d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
+    const float df = f32_trunc(d);
+    const float a = __shfl_sync(FULL, df, base), b = __shfl_sync(FULL, df, base + 1);
+    const float c = __shfl_sync(FULL, df, base + 2);
+    r2e = fmaf(c, c, fmaf(b, b, a * a));        // FP32 estimate: seeds 1/r before r2 is formed
     r2 = csum3(d * d, base);
     r2f = f32_trunc(r2);
   };
@@ -588,7 +616,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
     const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
     const double g = fz ? 0.0 : ghs;
-    const double ri = rsq_pair(r2);
+    const double ri = rsq_est(r2, r2e);
     const double xw = fma(r2 * ri, A, B);
     // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
     const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
@@ -648,9 +676,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   double rbi = 0.0, rb2 = 0.0, rb3 = 0.0;
   float rbf2 = 0.0f;
   auto body_r = [&]() {
+    const float xf = f32_trunc(X);
+    const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
+    const float c = __shfl_sync(FULL, xf, base + 2);
+    rbf2 = fmaf(c, c, fmaf(b, b, a * a));
     const double rr = csum3(X * X, base);
-    rbf2 = f32_trunc(rr);
-    rbi = rsq_pair(rr);
+    rbi = rsq_est(rr, rbf2);
     rb2 = rbi * rbi;
     rb3 = rb2 * rbi;
   };
@@ -726,15 +757,16 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
       const bool far = far_apart(U);
       const unsigned ord = drift_order();
+      // the order-2 drift, computed while the two decisions above are pending
+      const double fm1 = munht2 * rb3, fd = munh * rb3;
+      const double Xn = fma(fm1, X, fma(h, V, X));
+      const double Vn = fma(fd, X, fma(fm1, V, V));
       if (far && ord == 2u) {
         // the common sub-step as one straight block: F_j stays empty, series of order 2,
         // closing force and kick, and the next distances from the sun
         plev = j - 1;
-        const double X1 = fma(h, V, X);
-        const double fm1 = munht2 * rb3, fd = munh * rb3;
-        const double Xn = fma(fm1, X, X1);
-        V = fma(fd, X, fma(fm1, V, V));
         X = Xn;
+        V = Vn;
         sep();
         forces();
         V = fma(hc, d, V);
