@@ -36,9 +36,11 @@ FLOPS_PER_PAIR_CHECK = 18
 # sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
 # (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
 DFMA_LATENCY_CYCLES = 64.3
-FP64_INSTR_PER_CHAIN_SUBSTEP = 37.5
-# the trapezoid kick kernel at N = 10,000, one ncu capture (kick 1): DRAM read + write per launch
-KICK_TRAFFIC_BYTES_N10000 = (1.829120 + 14.927104) * 1e6
+FP64_INSTR_PER_CHAIN_SUBSTEP = 39.8
+# DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
+# trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
+KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.59) + (1.40 + 12.17)) / 2 * 1e6
+RECURSION_TRAFFIC_BYTES_N10000 = 1.93e6 + 11.78e3
 
 
 def parse():
@@ -300,7 +302,8 @@ def run_ours(args):
         roofline = {"kernel": "k_recursion (per-group recursive sub-stepping)", "bound": "alu",
                     "achieved": chain_achieved, "peak": chain_peak,
                     "unit": "M FP64 warp-instr/s on the longest group chain (one warp)",
-                    "frac": chain_achieved / chain_peak, "traffic": None,
+                    "frac": chain_achieved / chain_peak,
+                    "traffic": RECURSION_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
                     "share_of_step": phase_tot[5] / phase_tot.sum(),
                     "peak_source": f"SM clock {sm_hz / 1e6:.0f} MHz / {DFMA_LATENCY_CYCLES} cycles per "
                                    "dependent FP64 instruction (measured)",
@@ -312,7 +315,7 @@ def run_ours(args):
         roofline_kick = {"kernel": "k_trap_fp64 (trapezoid pair kick)", "bound": "alu", "achieved": kick_achieved,
                          "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                          "frac": kick_achieved / FP64_PEAK_TFLOPS_NOMINAL,
-                         "traffic": KICK_TRAFFIC_BYTES_N10000 if args.n == 10000 and prec == 0 else None,
+                         "traffic": KICK_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
                          "ms_per_launch": kick_ms, "peak_source": peak_note}
         phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
         cb = None
