@@ -754,36 +754,46 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       deepest = max(deepest, j);
       if (fat != j) { forces_skip(); fat = j; }
       const double U = V;                  // velocities the check sees
-      V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
-      const bool far = far_apart(U);
-      const unsigned ord = drift_order();
-      // the order-2 drift, computed while the two decisions above are pending
-      const double fm1 = munht2 * rb3, fd = munh * rb3;
-      const double Xn = fma(fm1, X, fma(h, V, X));
-      const double Vn = fma(fd, X, fma(fm1, V, V));
-      if (far && ord == 2u) {
-        // the common sub-step as one straight block: F_j stays empty, series of order 2,
-        // closing force and kick, and the next distances from the sun
-        plev = j - 1;
-        X = Xn;
-        V = Vn;
-        sep();
-        forces();
-        V = fma(hc, d, V);
-        body_r();
-        fat = j;
-        if (++cj < C.M) continue;
-        level_done = true;
-      } else {
-        const bool fl = !far && check_exact(U);
-        plev = fl ? j : j - 1;
-        const bool deeper = fl && (j + 1 <= C.max_depth);
-        if (fl && !deeper && lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
-        if (!deeper) {
-          drift(ord);
+      if (!fz) V = fma(hc, d, V);          // opening kick
+      bool fl = lt_nn(r2, R2);             // inside R_j: the pair is in F_j
+      if (!fl) {
+        const bool far = far_apart(U);
+        const unsigned ord = drift_order();
+        // the order-2 drift, computed while the two decisions above are pending
+        const double fm1 = munht2 * rb3, fd = munh * rb3;
+        const double Xn = fma(fm1, X, fma(h, V, X));
+        const double Vn = fma(fd, X, fma(fm1, V, V));
+        if (far && ord <= 3u) {
+          // the common sub-step as one straight block: F_j stays empty, series of order 2 or
+          // 3, closing force and kick, and the next distances from the sun
+          plev = j - 1;
+          if (ord == 2u) {
+            X = Xn;
+            V = Vn;
+          } else {
+            drift(3u);
+          }
           sep();
+          forces();
+          V = fma(hc, d, V);
           body_r();
+          fat = j;
+          if (++cj < C.M) continue;
+          level_done = true;
         } else {
+          fl = !far && check_exact(U);
+          if (!fl) {
+            plev = j - 1;
+            drift(ord);
+            sep();
+            body_r();
+            start = false;
+          }
+        }
+      }
+      if (fl) {
+        plev = j;
+        if (j + 1 <= C.max_depth) {
           cs[j] = cj;
           ++j;
           hs[j] = sub_interval(C, hs[j - 1]);
@@ -791,13 +801,17 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           set_level(j);
           continue;
         }
+        if (lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
+        drift(drift_order());
+        sep();
+        body_r();
         start = false;
       }
     }
     if (!level_done) {
       forces_skip();
       fat = j;
-      V = fma(hc, d, V);
+      if (!fz) V = fma(hc, d, V);
       if (++cj < C.M) { start = true; continue; }
     }
     --j;
