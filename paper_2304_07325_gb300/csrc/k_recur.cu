@@ -548,6 +548,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   const unsigned mb = pb ? 0xffffffffu : 0u;
   const DiskDesc *dp = C.dp;
   const double mu = C.mu;
+  // group constants in registers (the loop stores through hs and cs, which could alias C)
+  const int cM = C.M, cmax_sub = C.max_substeps, cmax_depth = C.max_depth, cd = C.d;
+  const double c_invM = C.invM;
+  const bool c_pow2 = (cM & (cM - 1)) == 0;
   const float muf = f32_trunc(mu);
   double X = Xio, V = Vio;
   long long substeps = substeps_io;
@@ -671,15 +675,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     return is_neg(e) || lt_nn(e, R2);
   };
 
-  // distance of this lane's body from the sun at the current positions: 1/r, 1/r^2, 1/r^3 and
-  // r^2 in FP32, computed right after every drift so that it overlaps the pair's force chain
+  // distance of this lane's body from the sun at the current positions: 1/r, 1/r^2, 1/r^3,
+  // computed at the opening of a sub-step, where it overlaps the FP32 decisions
   double rbi = 0.0, rb2 = 0.0, rb3 = 0.0;
-  float rbf2 = 0.0f;
   auto body_r = [&]() {
     const float xf = f32_trunc(X);
     const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
     const float c = __shfl_sync(FULL, xf, base + 2);
-    rbf2 = fmaf(c, c, fmaf(b, b, a * a));
+    const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
     const double rr = csum3(X * X, base);
     rbi = rsq_est(rr, rbf2);
     rb2 = rbi * rbi;
@@ -694,9 +697,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float x2f = __shfl_sync(FULL, xf, base + 2);
     const float v0 = __shfl_sync(FULL, vf, base), v1 = __shfl_sync(FULL, vf, base + 1);
     const float v2f = __shfl_sync(FULL, vf, base + 2);
+    const float rrf = fmaf(x2f, x2f, fmaf(x1, x1, x0 * x0));
     const float rvf = fmaf(x2f, v2f, fmaf(x1, v1, x0 * v0));
     const float vvf = fmaf(v2f, v2f, fmaf(v1, v1, v0 * v0));
-    const float rif = rsqrtf(rbf2), ri2f = rif * rif;
+    const float rif = rsqrtf(rrf), ri2f = rif * rif;
     const float uf = muf * ri2f * rif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
@@ -732,7 +736,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       double bvx = SH(V, base), bvy = SH(V, base + 1), bvz = SH(V, base + 2);
       if (!drift_series(mu, h, bx, by, bz, bvx, bvy, bvz)) {
         const int st = kepler_drift(mu, h, bx, by, bz, bvx, bvy, bvz);
-        if (st != SYMBA_OK && pc == 0 && cp == 0) set_status(&D.stat[C.d], st);
+        if (st != SYMBA_OK && pc == 0 && cp == 0) set_status(&D.stat[cd], st);
       }
       __syncwarp();
       X = pc == 0 ? bx : (pc == 1 ? by : (pc == 2 ? bz : 0.0));
@@ -745,18 +749,29 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   bool start = true;
   set_level(j);
   sep();
-  body_r();
   for (;;) {
     bool level_done = false;
     if (start) {
-      if (lt_nn(r2, pRcut)) { rc = 1; break; }
-      if (++substeps > C.max_substeps) { rc = 2; break; }
+      {
+        const bool touch = lt_nn(r2, pRcut);
+        if (touch || substeps >= cmax_sub) {     // both rare: one branch
+          if (touch) {
+            rc = 1;
+          } else {
+            ++substeps;
+            rc = 2;
+          }
+          break;
+        }
+      }
+      ++substeps;
       deepest = max(deepest, j);
       if (fat != j) { forces_skip(); fat = j; }
       const double U = V;                  // velocities the check sees
       if (!fz) V = fma(hc, d, V);          // opening kick
       bool fl = lt_nn(r2, R2);             // inside R_j: the pair is in F_j
       if (!fl) {
+        body_r();
         const bool far = far_apart(U);
         const unsigned ord = drift_order();
         // the order-2 drift, computed while the two decisions above are pending
@@ -776,9 +791,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           sep();
           forces();
           V = fma(hc, d, V);
-          body_r();
           fat = j;
-          if (++cj < C.M) continue;
+          if (++cj < cM) continue;
           level_done = true;
         } else {
           fl = !far && check_exact(U);
@@ -786,25 +800,24 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
             plev = j - 1;
             drift(ord);
             sep();
-            body_r();
             start = false;
           }
         }
       }
       if (fl) {
         plev = j;
-        if (j + 1 <= C.max_depth) {
+        if (j + 1 <= cmax_depth) {
           cs[j] = cj;
           ++j;
-          hs[j] = sub_interval(C, hs[j - 1]);
+          hs[j] = c_pow2 ? hs[j - 1] * c_invM : hs[j - 1] / (double)cM;
           cj = 0;
           set_level(j);
           continue;
         }
-        if (lane == 0) set_status(&D.stat[C.d], SYMBA_E_DEPTH);
+        if (lane == 0) set_status(&D.stat[cd], SYMBA_E_DEPTH);
+        body_r();
         drift(drift_order());
         sep();
-        body_r();
         start = false;
       }
     }
@@ -812,7 +825,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       forces_skip();
       fat = j;
       if (!fz) V = fma(hc, d, V);
-      if (++cj < C.M) { start = true; continue; }
+      if (++cj < cM) { start = true; continue; }
     }
     --j;
     fat = -1;
