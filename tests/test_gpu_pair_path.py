@@ -62,6 +62,17 @@ def _run(orc, sy, x, v, m, radius, steps):
     return ref, gpu, out
 
 
+def _binary():
+    m = np.array([3e-9, 2e-9])
+    G = 4.0 * np.pi ** 2
+    sep = 1e-4
+    vrel = np.sqrt(G * m.sum() / sep)
+    x = np.array([[1.0, 0.0, 0.0], [1.0 + sep, 0.0, 0.0]])
+    vc = np.array([0.0, 2.0 * np.pi, 0.0])
+    v = np.array([vc - [0.0, vrel * m[1] / m.sum(), 0.0], vc + [0.0, vrel * m[0] / m.sum(), 0.0]])
+    return x, v, m, np.array([2e-7, 2e-7])
+
+
 def test_bound_pair_group(orc, sy):
     d = disk.planetesimal_disk(10000, 1002)
     g = BOUND_PAIR_GROUP
@@ -76,14 +87,7 @@ def test_bound_pair_group(orc, sy):
 
 def test_isolated_tight_binary(orc, sy):
     """Two planetesimals 1e-4 AU apart on a mutual orbit at 1 AU: deep recursion every step."""
-    m = np.array([3e-9, 2e-9])
-    G = 4.0 * np.pi ** 2
-    sep = 1e-4
-    vrel = np.sqrt(G * m.sum() / sep)
-    x = np.array([[1.0, 0.0, 0.0], [1.0 + sep, 0.0, 0.0]])
-    vc = np.array([0.0, 2.0 * np.pi, 0.0])
-    v = np.array([vc - [0.0, vrel * m[1] / m.sum(), 0.0], vc + [0.0, vrel * m[0] / m.sum(), 0.0]])
-    radius = np.array([2e-7, 2e-7])
+    x, v, m, radius = _binary()
     ref, gpu, out = _run(orc, sy, x, v, m, radius, 3)
     for st, calls, depth, rel in out:
         assert depth >= 6 and st.max_depth == depth and st.substeps == calls
@@ -110,3 +114,41 @@ def test_pair_on_collision_course_merges(orc, sy):
     k = int(np.argmax(ag))
     assert np.linalg.norm(xg[k] - ref.x[k]) <= 1e-12 * np.linalg.norm(ref.x[k])
     assert np.linalg.norm(vg[k] - ref.v[k]) <= 1e-10 * np.linalg.norm(ref.v[k])
+
+
+def test_depth_limit_inside_the_pair_path(orc, sy):
+    """The binary needs depth 7; with max_depth = 4 the path reports SYMBA_E_DEPTH and, like the
+    oracle, drifts the pair at the deepest allowed level: same sub-steps, same positions."""
+    x, v, m, radius = _binary()
+    ref = orc.OracleSim(x, v, m, radius, params=orc.make_params(max_depth=4))
+    gpu = sy.System(x, v, m, radius, rhill=ref.rhill, params=sy.default_params(max_depth=4))
+    twin = orc.OracleSim(x, v, m, radius, rhill=ref.rhill, params=orc.make_params(max_depth=4, noise=1))
+    assert ref.step(1) == orc.E_DEPTH
+    twin.step(1)
+    gpu.step(1)
+    with pytest.raises(sy.SymbaError) as e:
+        gpu.sync()
+    assert e.value.code == sy.SYMBA_E_DEPTH
+    # the sticky status makes the synchronising calls report the error; the data is still copied
+    st = gpu.stats()
+    assert st.status == sy.SYMBA_E_DEPTH
+    assert st.max_depth == ref.max_depth_seen == 4
+    assert st.substeps == sum(ref.level_calls[1:])
+    xg, vg = np.zeros((2, 3)), np.zeros((2, 3))
+    assert sy.lib().symba_get_state(gpu._h, sy._ptr(xg), sy._ptr(vg), None, None, None) == sy.SYMBA_E_DEPTH
+    _close(xg, ref, twin)
+
+
+def test_substep_budget_inside_the_pair_path(sy):
+    """A sub-step budget far below the binary's 21,844 sub-steps per step: SYMBA_E_DEPTH, and the
+    context is usable again once a state is set."""
+    x, v, m, radius = _binary()
+    s = sy.System(x, v, m, radius, params=sy.default_params(max_substeps=100))
+    s.step(1)
+    with pytest.raises(sy.SymbaError) as e:
+        s.sync()
+    assert e.value.code == sy.SYMBA_E_DEPTH
+    assert s.stats().substeps == 101
+    s.set_state(x, v)
+    assert s.sync() == sy.SYMBA_OK
+    s.close()
