@@ -599,6 +599,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // separation x_b - x_a (this lane's component), its square norm, and that in FP32 (not above)
   double d = 0.0, r2 = 0.0;
   float r2f = 0.0f, r2e = 0.0f;
+  double c_r = 0.0, c_ri3 = 0.0;
+  bool rcache = false;          // c_r, c_ri3 hold r and 1/r^3 of the current positions
   auto sep = [&]() {
     const double Xo = __shfl_xor_sync(FULL, X, 4);
     d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
@@ -608,6 +610,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     r2e = fmaf(c, c, fmaf(b, b, a * a));        // FP32 estimate: seeds 1/r before r2 is formed
     r2 = csum3(d * d, base);
     r2f = f32_trunc(r2);
+    rcache = false;
   };
 
   // level-j force: hc = (h/2) w_j(r) G m_other / r^3 with this body's sign, zero when w_j
@@ -620,8 +623,16 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
     const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
     const double g = fz ? 0.0 : ghs;
-    const double ri = rsq_est(r2, r2e);
-    const double xw = fma(r2 * ri, A, B);
+    // r and 1/r^3 are level-independent: on entering a deeper level at unchanged positions the
+    // last ones are reused and only the weight is new
+    double ri = 0.0, r;
+    if (rcache) {
+      r = c_r;
+    } else {
+      ri = rsq_est(r2, r2e);
+      r = r2 * ri;
+    }
+    const double xw = fma(r, A, B);
     // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
     const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
@@ -629,7 +640,11 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     // [+-x^4 | x^2 qa + qb | 1/r^3]  (the sign of x^4 picks f or 1 - f)
     const double x2s = inner ? x2 : neg(x2);
     const double s2 = fma4(m0, m1, x2s, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2s, x2, -0.0);
-    const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
+    const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1);
+    const double ri3 = rcache ? c_ri3 : cpy(s2, lane, 2);
+    c_r = r;
+    c_ri3 = ri3;
+    rcache = true;
     // no clamp of x to [0, 1]: outside [R_{j+1}, R_{j-1}) the weight is zero (fz, x = 0 above),
     // inside x leaves [0, 1] only by rounding, where f_3 (flat at both ends) differs from 0 or
     // 1 by O(x^4) or O((x - 1)^2)
@@ -656,9 +671,11 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float sa = (__shfl_sync(FULL, av, base) + __shfl_sync(FULL, av, base + 1)) +
                      __shfl_sync(FULL, av, base + 2);
     const float m = 1.0f + 3.0517578e-5f;                       // 1 + 2^-15
-    const float dvmag = sqrtf(s2) * m + sa * 2.3841858e-7f;      // |dv| + truncation error (2^-22)
-    const float dlo = sqrtf(r2f) * (1.0f - 3.0517578e-5f);
-    const float rhs = (sqrtf(R2f) + dvmag * hf * m) * m;
+    // square roots as x rsqrt(x) (relative error below 2^-21, inside the margins; x = 0 gives
+    // NaN, which fails the test)
+    const float dvmag = s2 * rsqrtf(s2) * m + sa * 2.3841858e-7f;   // |dv| + truncation error (2^-22)
+    const float dlo = r2f * rsqrtf(r2f) * (1.0f - 3.0517578e-5f);
+    const float rhs = (R2f * rsqrtf(R2f) + dvmag * hf * m) * m;
     return R2f > 0.0f && dlo > rhs;                             // NaN and underflow: false
   };
   auto check_exact = [&](double U) -> bool {
