@@ -472,62 +472,50 @@ __device__ __forceinline__ double csum3(double p, int base) {
   const double c = __shfl_sync(FULL, p, base + 2);
   return (a + b) + c;
 }
-// The FP32 seed of 1/sqrt(r2) widened to FP64 (y0) and its exact square (t = y0^2, from the
-// 24-bit significand by an integer product), both without the FP64 pipe; false outside the
-// normal FP32 range.
-__device__ __forceinline__ bool rsqrt_seed_sq(double r2, double &y0, double &t) {
-  const int hi = __double2hiint(r2);
-  const unsigned lo = (unsigned)__double2loint(r2);
-  const int fe = ((hi >> 20) & 0x7FF) - 896;
-  if (!((unsigned)(fe - 1) <= 253u && hi > 0)) return false;
-  const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+// The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
+// FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
+// e = 1 - r2 t still reach full FP64 accuracy.  false when r2e is not a normal FP32 number.
+__device__ __forceinline__ bool seed_est(float r2e, double &y0, double &t) {
+  const unsigned yb = __float_as_uint(r2e);
+  const int fe = (int)((yb >> 23) & 0xFF);
+  if (!(fe >= 1 && fe <= 253 && (int)yb > 0)) return false;
   float y0f;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(((unsigned)fe << 23) | m23)));
-  const unsigned yb = __float_as_uint(y0f);
-  const int ey = (int)((yb >> 23) & 0xFF);
-  y0 = __hiloint2double(((ey + 896) << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
-  // y0 = my 2^(ey - 150) with my the 24-bit significand, so y0^2 = my^2 2^(2 ey - 300)
-  const unsigned long long my = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u);
-  const unsigned long long p = my * my;                       // in [2^46, 2^48)
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2e));
+  const unsigned b = __float_as_uint(y0f);
+  const int ey = (int)((b >> 23) & 0xFF);
+  y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
+  const unsigned long long my = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long p = my * my;
   const int top = (int)(p >> 47);
   const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
   const long long e2 = 2 * (ey - 127) + top + 1023;
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
   return true;
 }
-// The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
-// FP64 sum that forms r2: the seed's square t stays exact, so the third-order correction from
-// e = 1 - r2 t still reaches full FP64 accuracy.  Every lane of the warp must call it.
+// 1/sqrt(r2): y0 (1 + e/2 + 3e^2/8).  Every lane of the warp must call it.
 __device__ __forceinline__ double rsq_est(double r2, float r2e) {
-  const unsigned yb = __float_as_uint(r2e);
-  const int fe = (int)((yb >> 23) & 0xFF);
-  if (__all_sync(FULL, fe >= 1 && fe <= 253 && (int)yb > 0)) {
-    float y0f;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2e));
-    const unsigned b = __float_as_uint(y0f);
-    const int ey = (int)((b >> 23) & 0xFF);
-    const double y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
-    const unsigned long long my = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const unsigned long long p = my * my;
-    const int top = (int)(p >> 47);
-    const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
-    const long long e2 = 2 * (ey - 127) + top + 1023;
-    const double t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+  double y0 = 0.0, t = 0.0;
+  if (__all_sync(FULL, seed_est(r2e, y0, t))) {
     const double e = fma(-r2, t, 1.0);
     return fma(y0 * e, fma(e, 0.375, 0.5), y0);
   }
   return rsqrt(r2);
+}
+// r2^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8) to e^3 ~ 2^-62, with y0^3 = t y0;
+// also t and e, from which 1/r2 = t (1 + e + e^2).  Every lane of the warp must call it.
+__device__ __forceinline__ double rinv3_est(double r2, float r2e, double &t, double &e) {
+  double y0 = 0.0;
+  if (__all_sync(FULL, seed_est(r2e, y0, t))) {
+    e = fma(-r2, t, 1.0);
+    const double ty0 = t * y0;
+    return fma(ty0, e * fma(e, 1.875, 1.5), ty0);
+  }
+  const double ri = rsqrt(r2);
+  t = ri * ri;
+  e = 0.0;
+  return t * ri;
 }
 
-// 1/sqrt(r2), third-order correction of the seed (4 FP64 instructions)
-__device__ __forceinline__ double rsq_pair(double r2) {
-  double y0 = 0.0, t = 0.0;
-  if (rsqrt_seed_sq(r2, y0, t)) {
-    const double e = fma(-r2, t, 1.0);
-    return fma(y0 * e, fma(e, 0.375, 0.5), y0);
-  }
-  return rsqrt(r2);
-}
 
 // per-level constants of the single-pair path, cached in shared memory
 enum {
@@ -692,18 +680,15 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     return is_neg(e) || lt_nn(e, R2);
   };
 
-  // distance of this lane's body from the sun at the current positions: 1/r, 1/r^2, 1/r^3,
-  // computed at the opening of a sub-step, where it overlaps the FP32 decisions
-  double rbi = 0.0, rb2 = 0.0, rb3 = 0.0;
+  // distance of this lane's body from the sun at the current positions (1/r^3, and the pieces
+  // of 1/r^2), computed at the opening of a sub-step, where it overlaps the FP32 decisions
+  double rb3 = 0.0, rbt = 0.0, rbe = 0.0;    // 1/r^3; 1/r^2 = rbt (1 + rbe + rbe^2)
   auto body_r = [&]() {
     const float xf = f32_trunc(X);
     const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
     const float c = __shfl_sync(FULL, xf, base + 2);
     const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
-    const double rr = csum3(X * X, base);
-    rbi = rsq_est(rr, rbf2);
-    rb2 = rbi * rbi;
-    rb3 = rb2 * rbi;
+    rb3 = rinv3_est(csum3(X * X, base), rbf2, rbt, rbe);
   };
 
   // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
@@ -733,6 +718,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       X = Xn;
     } else if (ord == 3u) {
       const double rv = csum3(X * V, base);
+      const double rb2 = fma(rbt, fma(rbe, rbe, rbe), rbt);
       const double u = mu * rb3, p = rv * rb2;
       // [u p | -u/2 | -u/6]
       const double s3 = fma4(m0, m1, u, p, -0.0, u, -0.5, -0.0, u, -1.0 / 6.0, -0.0, u, p, -0.0);

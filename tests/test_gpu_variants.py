@@ -75,3 +75,22 @@ def test_variant_energy_conservation(sy):
         out[var["l"]] = abs((E1 - E0) / E0)
         s.close()
     assert out[1] < 1e-9 and out[3] < 1e-9
+
+
+def test_energy_error_second_order_in_tau(sy):
+    """The step is a second-order splitting: on the 100-body accuracy disk (no encounters), the
+    largest energy error over one orbit of the innermost body shrinks ~4x when tau halves."""
+    d = disk.hill_spaced_disk()
+    errs = []
+    for tau in (0.2, 0.1):
+        s = sy.System(d.x, d.v, d.m, d.radius, params=sy.default_params(dt=tau))
+        E0, _ = s.energy()
+        worst = 0.0
+        for _ in range(int(round(12.0 / tau / 10))):
+            s.step(10)
+            E, _ = s.energy()
+            worst = max(worst, abs((E - E0) / E0))
+        s.close()
+        errs.append(worst)
+    ratio = errs[0] / errs[1]
+    assert 3.0 < ratio < 5.5, (errs, ratio)
