@@ -475,12 +475,12 @@ __device__ __forceinline__ double csum3(double p, int base) {
 // The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
 // FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
 // e = 1 - r2 t still reach full FP64 accuracy.  false when r2e is not a normal FP32 number.
-__device__ __forceinline__ bool seed_est(float r2e, double &y0, double &t) {
+__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok) {
   const unsigned yb = __float_as_uint(r2e);
   const int fe = (int)((yb >> 23) & 0xFF);
-  if (!(fe >= 1 && fe <= 253 && (int)yb > 0)) return false;
+  ok = fe >= 1 && fe <= 253 && (int)yb > 0;
   float y0f;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2e));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(ok ? r2e : 1.0f));
   const unsigned b = __float_as_uint(y0f);
   const int ey = (int)((b >> 23) & 0xFF);
   y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
@@ -490,7 +490,11 @@ __device__ __forceinline__ bool seed_est(float r2e, double &y0, double &t) {
   const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
   const long long e2 = 2 * (ey - 127) + top + 1023;
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
-  return true;
+}
+__device__ __forceinline__ bool seed_est(float r2e, double &y0, double &t) {
+  bool ok;
+  seed_nb(r2e, y0, t, ok);
+  return ok;
 }
 // 1/sqrt(r2): y0 (1 + e/2 + 3e^2/8).  Every lane of the warp must call it.
 __device__ __forceinline__ double rsq_est(double r2, float r2e) {
@@ -500,6 +504,22 @@ __device__ __forceinline__ double rsq_est(double r2, float r2e) {
     return fma(y0 * e, fma(e, 0.375, 0.5), y0);
   }
   return rsqrt(r2);
+}
+// Branch-free forms for the straight common sub-step (a branch would end the block the
+// scheduler interleaves): ok reports whether the seed was in range; the caller votes on it and
+// takes the forms above when any lane was not.
+__device__ __forceinline__ double rsq_nb(double r2, float r2e, bool &ok) {
+  double y0, t;
+  seed_nb(r2e, y0, t, ok);
+  const double e = fma(-r2, t, 1.0);
+  return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+}
+__device__ __forceinline__ double rinv3_nb(double r2, float r2e, double &t, double &e, bool &ok) {
+  double y0;
+  seed_nb(r2e, y0, t, ok);
+  e = fma(-r2, t, 1.0);
+  const double ty0 = t * y0;
+  return fma(ty0, e * fma(e, 1.875, 1.5), ty0);
 }
 // r2^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8) to e^3 ~ 2^-62, with y0^3 = t y0;
 // also t and e, from which 1/r2 = t (1 + e + e^2).  Every lane of the warp must call it.
@@ -639,6 +659,30 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double w = fma(x4s, q, inner ? -0.0 : 1.0);
     hc = w * (ri3 * g);
   };
+  // the same for the straight block: no branch; f_ok = false when the seed was out of range
+  bool f_ok = true;
+  auto forces_nb = [&]() {
+    fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
+    const bool inner = lt_nn(r2, R2);
+    const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
+    const double g = fz ? 0.0 : ghs;
+    bool ok;
+    const double ri = rsq_nb(r2, r2e, ok);
+    f_ok = __all_sync(FULL, ok);
+    const double r = r2 * ri;
+    const double xw = fma(r, A, B);
+    const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
+    const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
+    const double ri2 = cpy(s1, lane, 3);
+    const double x2s = inner ? x2 : neg(x2);
+    const double s2 = fma4(m0, m1, x2s, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2s, x2, -0.0);
+    const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
+    const double w = fma(x4s, q, inner ? -0.0 : 1.0);
+    hc = w * (ri3 * g);
+    c_r = r;
+    c_ri3 = ri3;
+    rcache = f_ok;
+  };
   auto forces_skip = [&]() {
     fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
     if (fz) { hc = 0.0; return; }
@@ -683,12 +727,23 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // distance of this lane's body from the sun at the current positions (1/r^3, and the pieces
   // of 1/r^2), computed at the opening of a sub-step, where it overlaps the FP32 decisions
   double rb3 = 0.0, rbt = 0.0, rbe = 0.0;    // 1/r^3; 1/r^2 = rbt (1 + rbe + rbe^2)
+  bool rb_ok = true;
   auto body_r = [&]() {
     const float xf = f32_trunc(X);
     const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
     const float c = __shfl_sync(FULL, xf, base + 2);
     const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
     rb3 = rinv3_est(csum3(X * X, base), rbf2, rbt, rbe);
+    rb_ok = true;
+  };
+  auto body_r_nb = [&]() {                  // branch-free; rb_ok = false: take body_r()
+    const float xf = f32_trunc(X);
+    const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
+    const float c = __shfl_sync(FULL, xf, base + 2);
+    const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
+    bool ok;
+    rb3 = rinv3_nb(csum3(X * X, base), rbf2, rbt, rbe, ok);
+    rb_ok = __all_sync(FULL, ok);
   };
 
   // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
@@ -771,39 +826,52 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       deepest = max(deepest, j);
       if (fat != j) { forces_skip(); fat = j; }
       const double U = V;                  // velocities the check sees
-      if (!fz) V = fma(hc, d, V);          // opening kick
+      V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
       bool fl = lt_nn(r2, R2);             // inside R_j: the pair is in F_j
       if (!fl) {
-        body_r();
+        // one straight block: distances from the sun, the FP32 decisions and the order-2 drift
+        // they usually select
+        body_r_nb();
         const bool far = far_apart(U);
         const unsigned ord = drift_order();
-        // the order-2 drift, computed while the two decisions above are pending
         const double fm1 = munht2 * rb3, fd = munh * rb3;
         const double Xn = fma(fm1, X, fma(h, V, X));
         const double Vn = fma(fd, X, fma(fm1, V, V));
-        if (far && ord <= 3u) {
-          // the common sub-step as one straight block: F_j stays empty, series of order 2 or
-          // 3, closing force and kick, and the next distances from the sun
+        if (far && ord == 2u && rb_ok) {
+          // the common sub-step: F_j stays empty, series of order 2, closing force and kick
           plev = j - 1;
-          if (ord == 2u) {
-            X = Xn;
-            V = Vn;
-          } else {
-            drift(3u);
-          }
+          X = Xn;
+          V = Vn;
           sep();
-          forces();
-          V = fma(hc, d, V);
+          const double Vk = V;
+          forces_nb();
+          V = fma(hc, d, Vk);
+          if (!f_ok) {                      // a seed out of range: the general form
+            forces();
+            V = fma(hc, d, Vk);
+          }
           fat = j;
           if (++cj < cM) continue;
           level_done = true;
         } else {
-          fl = !far && check_exact(U);
-          if (!fl) {
+          if (!rb_ok) body_r();
+          if (far && ord <= 3u) {
             plev = j - 1;
             drift(ord);
             sep();
-            start = false;
+            forces();
+            V = fma(hc, d, V);
+            fat = j;
+            if (++cj < cM) continue;
+            level_done = true;
+          } else {
+            fl = !far && check_exact(U);
+            if (!fl) {
+              plev = j - 1;
+              drift(ord);
+              sep();
+              start = false;
+            }
           }
         }
       }
