@@ -607,8 +607,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // separation x_b - x_a (this lane's component), its square norm, and that in FP32 (not above)
   double d = 0.0, r2 = 0.0;
   float r2f = 0.0f, r2e = 0.0f;
-  double c_r = 0.0, c_ri3 = 0.0;
+  double c_r = 0.0, c_ri3 = 0.0, c_f = 0.0;
   bool rcache = false;          // c_r, c_ri3 hold r and 1/r^3 of the current positions
+  int c_lvl = -1;               // level of the last force at these positions, its weight c_f,
+  bool c_inner = false;         // and whether that weight was g (inside R_level, non-zero)
   auto sep = [&]() {
     const double Xo = __shfl_xor_sync(FULL, X, 4);
     d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
@@ -631,6 +633,15 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
     const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
     const double g = fz ? 0.0 : ghs;
+    if (rcache && c_lvl == j - 1 && c_inner && !inner && !fz) {
+      // entering level j at the positions of the last level-(j-1) force, with the pair between
+      // R_j and R_{j-1}: the weights telescope, w_j = 1 - g_{j-1}(r) = 1 - w_{j-1} (the same
+      // argument (r - R_j) / (R_{j-1} - R_j) in both), so only the products remain
+      hc = (1.0 - c_f) * (c_ri3 * g);
+      c_lvl = j;
+      c_inner = false;
+      return;
+    }
     // r and 1/r^3 are level-independent: on entering a deeper level at unchanged positions the
     // last ones are reused and only the weight is new
     double ri = 0.0, r;
@@ -658,6 +669,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     // 1 by O(x^4) or O((x - 1)^2)
     const double w = fma(x4s, q, inner ? -0.0 : 1.0);
     hc = w * (ri3 * g);
+    c_f = w;
+    c_lvl = j;
+    c_inner = inner && !fz;
   };
   // the same for the straight block: no branch; f_ok = false when the seed was out of range
   bool f_ok = true;
@@ -681,6 +695,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     hc = w * (ri3 * g);
     c_r = r;
     c_ri3 = ri3;
+    c_f = w;
+    c_lvl = j;
+    c_inner = inner && !fz;
     rcache = f_ok;
   };
   auto forces_skip = [&]() {
