@@ -21,7 +21,11 @@
 //     of the orbit; square roots come from an integer-built FP32 seed plus one FP64 correction;
 //     the shell weights use per-level reciprocal tables;
 //   - the forces of the closing kick of one sub-step are reused by the opening kick of the next
-//     (same positions, same pairs, same weights).
+//     (same positions, same pairs, same weights);
+//   - once F_{k-1} holds a single pair -- the close or bound pairs whose chains set the step
+//     time -- the sub-steps of levels >= k run in the single-pair path (pair_run), the two
+//     bodies packed component-wise across the warp (details at pair_run).
+// Groups of at most 32 bodies and 32 pairs keep their state in registers (run_group_regs).
 // The check below level 0 uses the division-free form of the predicate (same minimum-distance
 // test; identical except at exact ties).
 #include "internal.cuh"
