@@ -36,7 +36,7 @@ FLOPS_PER_PAIR_CHECK = 18
 # sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
 # (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
 DFMA_LATENCY_CYCLES = 64.3
-FP64_INSTR_PER_CHAIN_SUBSTEP = 35.6
+FP64_INSTR_PER_CHAIN_SUBSTEP = 36.1
 # DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
 # trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
 KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.59) + (1.40 + 12.17)) / 2 * 1e6
