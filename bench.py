@@ -39,8 +39,8 @@ DFMA_LATENCY_CYCLES = 64.3
 FP64_INSTR_PER_CHAIN_SUBSTEP = 36.1
 # DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
 # trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
-KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.59) + (1.40 + 12.17)) / 2 * 1e6
-RECURSION_TRAFFIC_BYTES_N10000 = 1.37e6 + 14.08e3
+KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.72) + (1.40 + 11.91)) / 2 * 1e6
+RECURSION_TRAFFIC_BYTES_N10000 = 1.99e6 + 11.01e3
 
 
 def parse():
