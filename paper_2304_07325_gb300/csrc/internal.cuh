@@ -138,22 +138,6 @@ __device__ __forceinline__ double rsqrt_fp64(double r2) {
   return rsqrt(r2);
 }
 
-// The FP32 seed of rsqrt_fp64 alone: built from the bits of r2 and widened back to FP64 by bit
-// operations; false (y0 untouched) when r2 is outside the normal FP32 range.
-__device__ __forceinline__ bool rsqrt_seed(double r2, double &y0) {
-  const int hi = __double2hiint(r2);
-  const unsigned lo = (unsigned)__double2loint(r2);
-  const int fe = ((hi >> 20) & 0x7FF) - 896;
-  if (!((unsigned)(fe - 1) <= 253u && hi > 0)) return false;
-  const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
-  float y0f;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(((unsigned)fe << 23) | m23)));
-  const unsigned yb = __float_as_uint(y0f);
-  const int ye = (int)((yb >> 23) & 0xFF) + 896;
-  y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
-  return true;
-}
-
 // Order of non-negative doubles through their bit patterns (an integer comparison instead of an
 // FP64-pipe one; valid for +0, finite and +inf operands).
 __device__ __forceinline__ bool lt_nn(double a, double b) {
@@ -218,18 +202,6 @@ __device__ __forceinline__ double partition_fn(double x, int l) {
   double xp = 1.0;
   for (int k = 0; k <= l; ++k) xp *= x;
   return xp * s;
-}
-
-// g_k(r): share of a pair force kept at levels <= k (1 outside R_k, 0 inside R_{k+1}).
-__device__ __forceinline__ double g_level(const DiskDesc &dd, double R0, int k, double r) {
-  const double Rk = R0 * dd.ck[k], Rk1 = R0 * dd.ck[k + 1];
-  return partition_fn((r - Rk1) / (Rk - Rk1), dd.l);
-}
-
-// Level-k weight of a pair force: w_0 = g_0, w_k = g_k - g_{k-1}.
-__device__ __forceinline__ double level_weight(const DiskDesc &dd, double R0, int k, double r) {
-  if (k == 0) return g_level(dd, R0, 0, r);
-  return g_level(dd, R0, k, r) - g_level(dd, R0, k - 1, r);
 }
 
 // --------------------------------------------------------------------------------------------
