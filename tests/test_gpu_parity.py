@@ -212,3 +212,27 @@ def test_benchmark_size_one_step(orc, sy):
     assert np.mean(rel <= 1e-12) > 0.99
     st = gpu.stats()
     assert st.max_depth == ref.max_depth_seen
+
+
+@pytest.mark.parametrize("n,seed", [(5000, 1001), (10000, 1002)])
+def test_benchmark_sizes_steps_from_oracle_states(orc, sy, n, seed):
+    """Both benchmark sizes (N = 5,000 and 10,000): two steps, each started from the oracle's
+    state, through the graph-replayed step the benchmark times; encounters bit-exact, positions
+    1e-12 relative (chaos-aware), same mergers."""
+    d = disk.planetesimal_disk(n, seed)
+    ref, gpu = _pair(orc, sy, d)
+    for _ in range(2):
+        gpu.set_state(ref.x, ref.v)
+        twin = _twin(orc, d, ref)
+        twin.alive[...] = ref.alive
+        twin.m[...] = ref.m
+        twin.radius[...] = ref.radius
+        twin.rhill[...] = ref.rhill
+        assert ref.step(1) >= 0 and twin.step(1) >= 0
+        gpu.step(1)
+        assert gpu.sync() >= 0
+        _same_groups(ref, gpu)
+        x, v, m, r, a = gpu.get_state()
+        assert np.array_equal(a, ref.alive) and np.array_equal(m, ref.m)
+        rel, spread = _check_positions(x, ref, twin)
+        assert np.mean(rel <= 1e-12) > 0.99
