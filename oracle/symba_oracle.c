@@ -241,7 +241,23 @@ int orc_encounter(const double *xi, const double *xj, const double *vi, const do
 /* Kepler drift: x, v advanced by dt on the two-body orbit of gravitational parameter mu,       */
 /* with Danby's f and g functions.  Elliptic case (alpha > 0) in eccentric-anomaly difference;  */
 /* alpha <= 0 in universal variables with Stumpff functions.  Returns ORC_OK or ORC_E_KEPLER.   */
+/* The new state is x0 + ((f - 1) x0 + g v0), v0 + (f' x0 + (g' - 1) v0): over the short        */
+/* intervals deep in the recursion f - 1 and g' - 1 (about -mu dt^2 / (2 r^3)) fall below half  */
+/* an ulp of 1, so f and g' formed as 1 + (...) would round to 1 and lose them at every call.   */
 /* ------------------------------------------------------------------------------------------ */
+
+/* X - sin X without cancellation: its Taylor series for |X| < 1/2 (terms to X^23, the next    */
+/* below 2^-60 of the first), X - sin X directly beyond.                                         */
+static double x_minus_sin(double X) {
+  if (fabs(X) >= 0.5) return X - sin(X);
+  double X2 = X * X, term = X * X2 / 6.0, s = 0.0;
+  for (int k = 1; k <= 11; ++k) {
+    s += term;
+    term *= -X2 / ((double)(2 * k + 2) * (double)(2 * k + 3));
+  }
+  return s;
+}
+
 static int drift_elliptic(double mu, double dt, double *x, double *v, double r0, double u,
                           double alpha) {
   double a = mu / alpha;
@@ -270,14 +286,14 @@ static int drift_elliptic(double mu, double dt, double *x, double *v, double r0,
   double sx = sin(X), sh = sin(0.5 * X);
   double omc = 2.0 * sh * sh;
   double r = a * (1.0 - ec * (1.0 - omc) + es * sx);
-  double f = 1.0 - (a / r0) * omc;
-  double g = dt - (X - sx) / n;
+  double fm1 = -(a / r0) * omc;
+  double g = dt - x_minus_sin(X) / n;
   double fdot = -(a * a * n * sx) / (r * r0);
-  double gdot = 1.0 - (a / r) * omc;
+  double gdm1 = -(a / r) * omc;
   double x0[3] = {x[0], x[1], x[2]}, v0[3] = {v[0], v[1], v[2]};
   for (int c = 0; c < 3; ++c) {
-    x[c] = f * x0[c] + g * v0[c];
-    v[c] = fdot * x0[c] + gdot * v0[c];
+    x[c] = x0[c] + (fm1 * x0[c] + g * v0[c]);
+    v[c] = v0[c] + (fdot * x0[c] + gdm1 * v0[c]);
   }
   return ORC_OK;
 }
@@ -347,14 +363,14 @@ static int drift_universal(double mu, double dt, double *x, double *v, double r0
   stumpff(alpha * s * s, c);
   double G1 = s * c[1], G2 = s * s * c[2], G3 = s * s * s * c[3];
   double r = r0 * c[0] + u * G1 + mu * G2;
-  double f = 1.0 - mu * G2 / r0;
+  double fm1 = -mu * G2 / r0;
   double g = dt - mu * G3;
   double fdot = -mu * G1 / (r * r0);
-  double gdot = 1.0 - mu * G2 / r;
+  double gdm1 = -mu * G2 / r;
   double x0[3] = {x[0], x[1], x[2]}, v0[3] = {v[0], v[1], v[2]};
   for (int k = 0; k < 3; ++k) {
-    x[k] = f * x0[k] + g * v0[k];
-    v[k] = fdot * x0[k] + gdot * v0[k];
+    x[k] = x0[k] + (fm1 * x0[k] + g * v0[k]);
+    v[k] = v0[k] + (fdot * x0[k] + gdm1 * v0[k]);
   }
   return ORC_OK;
 }
