@@ -15,7 +15,7 @@
 
 #define SYM_TILE 32
 #define SYM_MAX_LEVELS 32
-#define SYM_PAIR_LC (16 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
+#define SYM_PAIR_LC (17 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
 #define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
 
 struct DiskDesc {
@@ -320,6 +320,25 @@ __device__ inline void stumpff4(double z, double c[4]) {
   c[3] = (1.0 - c[1]) / z;
 }
 
+// X - sin X = X^3 (1/3! - X^2/5! + X^4/7! - ...) in Horner form for |X| < 1/2 (through X^19,
+// the rest below 1e-21 relative), where the direct difference loses digits to cancellation
+__device__ inline double x_minus_sin(double X) {
+  if (fabs(X) >= 0.5) return X - sin(X);
+  const double z = X * X;
+  double p = -1.0 / 121645100408832000.0;                       // -1/19!
+  p = fma(p, z, 1.0 / 355687428096000.0);                       // 1/17!
+  p = fma(p, z, -1.0 / 1307674368000.0);                        // -1/15!
+  p = fma(p, z, 1.0 / 6227020800.0);                            // 1/13!
+  p = fma(p, z, -1.0 / 39916800.0);                             // -1/11!
+  p = fma(p, z, 1.0 / 362880.0);                                // 1/9!
+  p = fma(p, z, -1.0 / 5040.0);                                 // -1/7!
+  p = fma(p, z, 1.0 / 120.0);                                   // 1/5!
+  p = fma(p, z, -1.0 / 6.0);                                    // -1/3!
+  return -(X * z) * p;
+}
+
+// The new state is x0 + ((f - 1) x0 + g v0), v0 + (f' x0 + (g' - 1) v0): f - 1 and g' - 1 are
+// formed apart from the 1, which they would be rounded into when small.
 __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, double &z,
                                    double &vx, double &vy, double &vz) {
   const double r0 = sqrt(fma(z, z, fma(y, y, x * x)));
@@ -327,7 +346,7 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
   const double u = fma(z, vz, fma(y, vy, x * vx));
   const double alpha = 2.0 * mu / r0 - v2;
   if (!(r0 > 0.0) || !isfinite(alpha) || !isfinite(u)) return SYMBA_E_NONFINITE;
-  double f, g, fdot, gdot;
+  double fm1, g, fdot, gdm1;
   if (alpha > 0.0) {
     const double a = mu / alpha;
     const double nn = sqrt(mu / (a * a * a));
@@ -369,10 +388,10 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
     sincos(X, &sx, &cx);
     const double omc = (cx > 0.0) ? sx * sx / (1.0 + cx) : 1.0 - cx;
     const double r = a * (1.0 - ec * cx + es * sx);
-    f = 1.0 - (a / r0) * omc;
-    g = dt - (X - sx) / nn;
+    fm1 = -(a / r0) * omc;
+    g = dt - x_minus_sin(X) / nn;
     fdot = -(a * a * nn * sx) / (r * r0);
-    gdot = 1.0 - (a / r) * omc;
+    gdm1 = -(a / r) * omc;
   } else {
     const double sgn = dt >= 0.0 ? 1.0 : -1.0;
     double c[4];
@@ -408,18 +427,18 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
     stumpff4(alpha * s * s, c);
     const double G1 = s * c[1], G2 = s * s * c[2], G3 = s * s * s * c[3];
     const double r = r0 * c[0] + u * G1 + mu * G2;
-    f = 1.0 - mu * G2 / r0;
+    fm1 = -mu * G2 / r0;
     g = dt - mu * G3;
     fdot = -mu * G1 / (r * r0);
-    gdot = 1.0 - mu * G2 / r;
+    gdm1 = -mu * G2 / r;
   }
   const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
-  x = f * x0 + g * vx0;
-  y = f * y0 + g * vy0;
-  z = f * z0 + g * vz0;
-  vx = fdot * x0 + gdot * vx0;
-  vy = fdot * y0 + gdot * vy0;
-  vz = fdot * z0 + gdot * vz0;
+  x = x0 + fma(fm1, x0, g * vx0);
+  y = y0 + fma(fm1, y0, g * vy0);
+  z = z0 + fma(fm1, z0, g * vz0);
+  vx = vx0 + fma(gdm1, vx0, fdot * x0);
+  vy = vy0 + fma(gdm1, vy0, fdot * y0);
+  vz = vz0 + fma(gdm1, vz0, fdot * z0);
   return SYMBA_OK;
 }
 

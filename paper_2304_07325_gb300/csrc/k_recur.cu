@@ -518,13 +518,6 @@ __device__ __forceinline__ double rsq_nb(double r2, float r2e, bool &ok) {
   const double e = fma(-r2, t, 1.0);
   return fma(y0 * e, fma(e, 0.375, 0.5), y0);
 }
-__device__ __forceinline__ double rinv3_nb(double r2, float r2e, double &t, double &e, bool &ok) {
-  double y0;
-  seed_nb(r2e, y0, t, ok);
-  e = fma(-r2, t, 1.0);
-  const double ty0 = t * y0;
-  return fma(ty0, e * fma(e, 1.875, 1.5), ty0);
-}
 // r2^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8) to e^3 ~ 2^-62, with y0^3 = t y0;
 // also t and e, from which 1/r2 = t (1 + e + e^2).  Every lane of the warp must call it.
 __device__ __forceinline__ double rinv3_est(double r2, float r2e, double &t, double &e) {
@@ -544,7 +537,7 @@ __device__ __forceinline__ double rinv3_est(double r2, float r2e, double &t, dou
 // per-level constants of the single-pair path, cached in shared memory
 enum {
   LC_H, LC_HH, LC_T2, LC_R2, LC_A1, LC_B1, LC_A2, LC_B2, LC_GHA, LC_GHB, LC_T3, LC_MUNH, LC_H15,
-  LC_MUNHT2, LC_R2N, LC_R2P, LC_N
+  LC_MUNH15, LC_R2N, LC_R2P, LC_MUNH1875, LC_N
 };
 
 // Runs the sub-steps of levels >= k with F_{k-1} = {q}, from the opening of a sub-step at level
@@ -557,6 +550,19 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
                                      long long &substeps_io, int &deepest_io) {
   const int pc = lane & 3, pb = (lane >> 2) & 1, cp = lane >> 3, base = lane & ~3;
   const unsigned m0 = (cp & 1) ? 0xffffffffu : 0u, m1 = (cp & 2) ? 0xffffffffu : 0u;
+  // the two packed stages of the shell weight, with their copy-dependent constants set once:
+  // stage1 = [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2], stage2 = [+-x^4 | x^2 qa + qb | 1/r^3 | +-x^4]
+  const unsigned mc0 = cp == 0 ? 0xffffffffu : 0u, mc1 = cp == 1 ? 0xffffffffu : 0u;
+  const unsigned mc2 = cp == 2 ? 0xffffffffu : 0u, mc3 = cp == 3 ? 0xffffffffu : 0u;
+  const double kb1 = cp == 1 ? -20.0 : -84.0, kc1 = cp == 1 ? 70.0 : (cp == 2 ? 35.0 : -0.0);
+  const double kd3 = cp == 1 ? -0.5 : -1.0 / 6.0;
+  auto stage1 = [&](double xw, double ri) {
+    return fma_rn(bsel(ri, xw, mc3), bsel(xw, bsel(ri, kb1, mc3), mc0), kc1);
+  };
+  auto stage2 = [&](double x2s, double x2, double qa, double qb, double ri2, double ri) {
+    return fma_rn(bsel(ri2, bsel(x2, x2s, mc1), mc2), bsel(ri, bsel(qa, x2, mc1), mc2),
+                  bsel(qb, -0.0, mc1));
+  };
   const unsigned mb = pb ? 0xffffffffu : 0u;
   const DiskDesc *dp = C.dp;
   const double mu = C.mu;
@@ -573,7 +579,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   unsigned long long have = 0ull;
 
   // current level's constants
-  double h, hh, t2, R2, A1, B1, A2, B2, ghs, t3, munh, h15, munht2, R2n, R2p;
+  double h, hh, t2, R2, A1, B1, A2, B2, ghs, t3, munh, h15, munh15, munh1875, R2n, R2p;
   float hf, R2f;
   auto set_level = [&](int jj) {
     double *Lc = lc + LC_N * jj;
@@ -588,13 +594,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
                              piR0, dp->invdc[jj - 1], -0.0, dp->ck[jj], dp->invdc[jj - 1], -0.0);
       // [G m_a h/2 | G m_b h/2 | h^3 | -mu h]
       const double s3 = fma4(m0, m1, gA, hh_, -0.0, gB, hh_, -0.0, t2_, hj, -0.0, mu, -hj, -0.0);
-      // [mu h/2 | 1.5 h | R_{j-1}^2]
+      // [mu h/2 | 1.5 h | R_{j-1}^2]; -mu h times the series coefficients of r^-3 below
       const double s4 = fma4(m0, m1, mu, hh_, -0.0, hh_, 1.0, hj, pR0sq, dp->ck2[jj - 1], -0.0,
                              mu, hh_, -0.0);
       const double v[LC_N] = {hj, hh_, t2_, cpy(s1, lane, 2), cpy(s2, lane, 0), -cpy(s2, lane, 1),
                               cpy(s2, lane, 2), -cpy(s2, lane, 3), cpy(s3, lane, 0),
                               cpy(s3, lane, 1), cpy(s3, lane, 2), cpy(s3, lane, 3), cpy(s4, lane, 1),
-                              cpy(s4, lane, 0) * -hj, cpy(s1, lane, 3), cpy(s4, lane, 2)};
+                              cpy(s3, lane, 3) * 1.5, cpy(s1, lane, 3), cpy(s4, lane, 2),
+                              cpy(s3, lane, 3) * 1.875};
 #pragma unroll
       for (int i = 0; i < LC_N; ++i) Lc[i] = v[i];
       have |= 1ull << jj;
@@ -602,7 +609,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     h = Lc[LC_H]; hh = Lc[LC_HH]; t2 = Lc[LC_T2]; R2 = Lc[LC_R2];
     A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
     ghs = pb ? -Lc[LC_GHA] : Lc[LC_GHB];
-    t3 = Lc[LC_T3]; munh = Lc[LC_MUNH]; h15 = Lc[LC_H15]; munht2 = Lc[LC_MUNHT2];
+    t3 = Lc[LC_T3]; munh = Lc[LC_MUNH]; h15 = Lc[LC_H15];
+    munh15 = Lc[LC_MUNH15]; munh1875 = Lc[LC_MUNH1875];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
     hf = f32_trunc(h);
     R2f = f32_trunc(R2) * (1.0f + 3.0517578e-5f);     // not below R2
@@ -657,12 +665,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     }
     const double xw = fma(r, A, B);
     // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
-    const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
+    const double s1 = stage1(xw, ri);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
     // [+-x^4 | x^2 qa + qb | 1/r^3]  (the sign of x^4 picks f or 1 - f)
     const double x2s = inner ? x2 : neg(x2);
-    const double s2 = fma4(m0, m1, x2s, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2s, x2, -0.0);
+    const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1);
     const double ri3 = rcache ? c_ri3 : cpy(s2, lane, 2);
     c_r = r;
@@ -689,11 +697,11 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     f_ok = __all_sync(FULL, ok);
     const double r = r2 * ri;
     const double xw = fma(r, A, B);
-    const double s1 = fma4(m0, m1, xw, xw, -0.0, xw, -20.0, 70.0, xw, -84.0, 35.0, ri, ri, -0.0);
+    const double s1 = stage1(xw, ri);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
     const double x2s = inner ? x2 : neg(x2);
-    const double s2 = fma4(m0, m1, x2s, x2, -0.0, x2, qa, qb, ri2, ri, -0.0, x2s, x2, -0.0);
+    const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
     const double w = fma(x4s, q, inner ? -0.0 : 1.0);
     hc = w * (ri3 * g);
@@ -747,7 +755,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // distance of this lane's body from the sun at the current positions (1/r^3, and the pieces
   // of 1/r^2), computed at the opening of a sub-step, where it overlaps the FP32 decisions
-  double rb3 = 0.0, rbt = 0.0, rbe = 0.0;    // 1/r^3; 1/r^2 = rbt (1 + rbe + rbe^2)
+  // 1/r^3; 1/r^2 = rbt (1 + rbe + rbe^2); body_r_nb() leaves rb3 to rb3_nb() and keeps rbty =
+  // y0^3 = rbt y0, so that 1/r^3 = rbty (1 + 3e/2 + 15e^2/8) with e = rbe
+  double rb3 = 0.0, rbt = 0.0, rbe = 0.0, rbty = 0.0;
   bool rb_ok = true;
   auto body_r = [&]() {
     const float xf = f32_trunc(X);
@@ -762,10 +772,15 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
     const float c = __shfl_sync(FULL, xf, base + 2);
     const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
+    const double rs2 = csum3(X * X, base);
+    double y0;
     bool ok;
-    rb3 = rinv3_nb(csum3(X * X, base), rbf2, rbt, rbe, ok);
+    seed_nb(rbf2, y0, rbt, ok);
+    rbe = fma(-rs2, rbt, 1.0);
+    rbty = rbt * y0;
     rb_ok = __all_sync(FULL, ok);
   };
+  auto rb3_nb = [&]() { rb3 = fma(rbty, rbe * fma(rbe, 1.875, 1.5), rbty); };
 
   // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
   // drift_series): 2, 3, 6, or 9 for the Kepler solver
@@ -786,18 +801,19 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // Kepler drift of both bodies over h: Lagrange series of order 2 or 3, else the scalar path
   auto drift = [&](unsigned ord) {
-    const double X1 = fma(h, V, X);
     if (ord == 2u) {
-      const double fm1 = munht2 * rb3, fd = munh * rb3;      // f - 1 = -mu h^2/(2 r^3), f' = -mu h/r^3
-      const double Xn = fma(fm1, X, X1);
-      V = fma(fd, X, fma(fm1, V, V));
-      X = Xn;
+      // f - 1 = f' h/2 with f' = -mu h/r^3: x' = (x + h/2 v) + h/2 (v + f' x), v' = v + f' (x + h/2 v)
+      const double fd = munh * rb3;
+      const double W = fma(fd, X, V), Y = fma(hh, V, X);
+      X = fma(hh, W, Y);
+      V = fma(fd, Y, V);
     } else if (ord == 3u) {
+      const double X1 = fma(h, V, X);
       const double rv = csum3(X * V, base);
       const double rb2 = fma(rbt, fma(rbe, rbe, rbe), rbt);
       const double u = mu * rb3, p = rv * rb2;
-      // [u p | -u/2 | -u/6]
-      const double s3 = fma4(m0, m1, u, p, -0.0, u, -0.5, -0.0, u, -1.0 / 6.0, -0.0, u, p, -0.0);
+      // [u p | -u/2 | -u/6 | u p]
+      const double s3 = u * bsel(kd3, p, mc1 | mc2);
       const double up = cpy(s3, lane, 0), nhu = cpy(s3, lane, 1), nu6 = cpy(s3, lane, 2);
       // [h/2 up - u/2 | 1.5 h up - u | h up - u/2 | -u h^3/6]
       const double s4 = fma4(m0, m1, hh, up, nhu, h15, up, -u, h, up, nhu, t3, nu6, -0.0);
@@ -855,9 +871,11 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         body_r_nb();
         const bool far = far_apart(U);
         const unsigned ord = drift_order();
-        const double fm1 = munht2 * rb3, fd = munh * rb3;
-        const double Xn = fma(fm1, X, fma(h, V, X));
-        const double Vn = fma(fd, X, fma(fm1, V, V));
+        // the order-2 drift as in drift(2), with f' = -mu h/r^3 straight from the seed terms
+        const double fd = rbty * fma(rbe, fma(rbe, munh1875, munh15), munh);
+        const double W = fma(fd, X, V), Y = fma(hh, V, X);
+        const double Xn = fma(hh, W, Y);
+        const double Vn = fma(fd, Y, V);
         if (far && ord == 2u && rb_ok) {
           // the common sub-step: F_j stays empty, series of order 2, closing force and kick
           plev = j - 1;
@@ -875,7 +893,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           if (++cj < cM) continue;
           level_done = true;
         } else {
-          if (!rb_ok) body_r();
+          if (rb_ok) rb3_nb(); else body_r();
           if (far && ord <= 3u) {
             plev = j - 1;
             drift(ord);
