@@ -479,11 +479,10 @@ __device__ __forceinline__ double csum3(double p, int base) {
 // The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
 // FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
 // e = 1 - r2 t still reach full FP64 accuracy.  false when r2e is not a normal FP32 number.
-__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok) {
+__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok, float &y0f) {
   const unsigned yb = __float_as_uint(r2e);
   const int fe = (int)((yb >> 23) & 0xFF);
   ok = fe >= 1 && fe <= 253 && (int)yb > 0;
-  float y0f;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(ok ? r2e : 1.0f));
   const unsigned b = __float_as_uint(y0f);
   const int ey = (int)((b >> 23) & 0xFF);
@@ -494,6 +493,10 @@ __device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &
   const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
   const long long e2 = 2 * (ey - 127) + top + 1023;
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+}
+__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok) {
+  float y0f;
+  seed_nb(r2e, y0, t, ok, y0f);
 }
 __device__ __forceinline__ bool seed_est(float r2e, double &y0, double &t) {
   bool ok;
@@ -564,6 +567,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
                   bsel(qb, -0.0, mc1));
   };
   const unsigned mb = pb ? 0xffffffffu : 0u;
+  const long long sgn_a = pb ? 0ll : (long long)0x8000000000000000ull;    // sign flip on body a
+  const long long sgn_b = pb ? (long long)0x8000000000000000ull : 0ll;    // and on body b
+  auto flip = [](double v, long long s) { return __longlong_as_double(__double_as_longlong(v) ^ s); };
   const DiskDesc *dp = C.dp;
   const double mu = C.mu;
   // group constants in registers (the loop stores through hs and cs, which could alias C)
@@ -619,13 +625,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // separation x_b - x_a (this lane's component), its square norm, and that in FP32 (not above)
   double d = 0.0, r2 = 0.0;
   float r2f = 0.0f, r2e = 0.0f;
-  double c_r = 0.0, c_ri3 = 0.0, c_f = 0.0;
-  bool rcache = false;          // c_r, c_ri3 hold r and 1/r^3 of the current positions
+  double c_ri = 0.0, c_ri3 = 0.0, c_f = 0.0;
+  bool rcache = false;          // c_ri, c_ri3 hold 1/r and 1/r^3 of the current positions
   int c_lvl = -1;               // level of the last force at these positions, its weight c_f,
   bool c_inner = false;         // and whether that weight was g (inside R_level, non-zero)
   auto sep = [&]() {
+    // x_b - x_a on both bodies' lanes as a sum of sign-flipped operands (exactly X - Xo, Xo - X)
     const double Xo = __shfl_xor_sync(FULL, X, 4);
-    d = bsel(X, Xo, mb) - bsel(Xo, X, mb);
+    d = flip(X, sgn_a) + flip(Xo, sgn_b);
     const float df = f32_trunc(d);
     const float a = __shfl_sync(FULL, df, base), b = __shfl_sync(FULL, df, base + 1);
     const float c = __shfl_sync(FULL, df, base + 2);
@@ -654,16 +661,11 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       c_inner = false;
       return;
     }
-    // r and 1/r^3 are level-independent: on entering a deeper level at unchanged positions the
-    // last ones are reused and only the weight is new
-    double ri = 0.0, r;
-    if (rcache) {
-      r = c_r;
-    } else {
-      ri = rsq_est(r2, r2e);
-      r = r2 * ri;
-    }
-    const double xw = fma(r, A, B);
+    // 1/r and 1/r^3 are level-independent: on entering a deeper level at unchanged positions
+    // the last ones are reused and only the weight is new.  The weight argument r A + B is
+    // formed as (1/r)(r^2 A) + B, so that r^2 A is ready before the reciprocal square root.
+    const double ri = rcache ? c_ri : rsq_est(r2, r2e);
+    const double xw = fma(ri, r2 * A, B);
     // f_3(x) = x^4 ((35 - 84 x) + x^2 (70 - 20 x)):  [x^2 | 70 - 20 x | 35 - 84 x | 1/r^2]
     const double s1 = stage1(xw, ri);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
@@ -673,7 +675,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1);
     const double ri3 = rcache ? c_ri3 : cpy(s2, lane, 2);
-    c_r = r;
+    c_ri = ri;
     c_ri3 = ri3;
     rcache = true;
     // no clamp of x to [0, 1]: outside [R_{j+1}, R_{j-1}) the weight is zero (fz, x = 0 above),
@@ -695,8 +697,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     bool ok;
     const double ri = rsq_nb(r2, r2e, ok);
     f_ok = __all_sync(FULL, ok);
-    const double r = r2 * ri;
-    const double xw = fma(r, A, B);
+    const double xw = fma(ri, r2 * A, B);
     const double s1 = stage1(xw, ri);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
@@ -705,7 +706,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
     const double w = fma(x4s, q, inner ? -0.0 : 1.0);
     hc = w * (ri3 * g);
-    c_r = r;
+    c_ri = ri;
     c_ri3 = ri3;
     c_f = w;
     c_lvl = j;
@@ -767,15 +768,17 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     rb3 = rinv3_est(csum3(X * X, base), rbf2, rbt, rbe);
     rb_ok = true;
   };
+  float bx0 = 0.0f, bx1 = 0.0f, bx2 = 0.0f, brif = 0.0f;   // FP32 copies of x and 1/|x| (seed)
   auto body_r_nb = [&]() {                  // branch-free; rb_ok = false: take body_r()
     const float xf = f32_trunc(X);
-    const float a = __shfl_sync(FULL, xf, base), b = __shfl_sync(FULL, xf, base + 1);
-    const float c = __shfl_sync(FULL, xf, base + 2);
-    const float rbf2 = fmaf(c, c, fmaf(b, b, a * a));
+    bx0 = __shfl_sync(FULL, xf, base);
+    bx1 = __shfl_sync(FULL, xf, base + 1);
+    bx2 = __shfl_sync(FULL, xf, base + 2);
+    const float rbf2 = fmaf(bx2, bx2, fmaf(bx1, bx1, bx0 * bx0));
     const double rs2 = csum3(X * X, base);
     double y0;
     bool ok;
-    seed_nb(rbf2, y0, rbt, ok);
+    seed_nb(rbf2, y0, rbt, ok, brif);
     rbe = fma(-rs2, rbt, 1.0);
     rbty = rbt * y0;
     rb_ok = __all_sync(FULL, ok);
@@ -795,6 +798,18 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float vvf = fmaf(v2f, v2f, fmaf(v1, v1, v0 * v0));
     const float rif = rsqrtf(rrf), ri2f = rif * rif;
     const float uf = muf * ri2f * rif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
+    const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
+    return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
+  };
+  // the same decision from the FP32 copies and the seed body_r_nb() took (valid when rb_ok)
+  auto drift_order_nb = [&]() -> unsigned {
+    const float vf = f32_trunc(V);
+    const float v0 = __shfl_sync(FULL, vf, base), v1 = __shfl_sync(FULL, vf, base + 1);
+    const float v2f = __shfl_sync(FULL, vf, base + 2);
+    const float rvf = fmaf(bx2, v2f, fmaf(bx1, v1, bx0 * v0));
+    const float vvf = fmaf(v2f, v2f, fmaf(v1, v1, v0 * v0));
+    const float ri2f = brif * brif;
+    const float uf = muf * ri2f * brif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
   };
@@ -870,7 +885,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         // they usually select
         body_r_nb();
         const bool far = far_apart(U);
-        const unsigned ord = drift_order();
+        unsigned ord = drift_order_nb();
         // the order-2 drift as in drift(2), with f' = -mu h/r^3 straight from the seed terms
         const double fd = rbty * fma(rbe, fma(rbe, munh1875, munh15), munh);
         const double W = fma(fd, X, V), Y = fma(hh, V, X);
@@ -893,7 +908,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           if (++cj < cM) continue;
           level_done = true;
         } else {
-          if (rb_ok) rb3_nb(); else body_r();
+          if (rb_ok) {
+            rb3_nb();
+          } else {
+            body_r();
+            ord = drift_order();
+          }
           if (far && ord <= 3u) {
             plev = j - 1;
             drift(ord);
