@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--n-hi", type=int, default=10000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--steps-cap", type=int, default=40)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched mode: keep the default launch schedule instead of autotuning it")
     return ap.parse_args()
 
 
@@ -369,6 +371,9 @@ def run_batched(args):
         pool.admit(d.x, d.v, d.m, d.radius)
     pool.step(args.warmup)
     pool.sync()
+    # launch schedules timed on this pool (state left as it was), the fastest kept
+    tune = None if args.no_autotune else pool.autotune(reps=3)
+    schedule = pool.schedule
     clocks = ClockSampler(0)
     torch.cuda.synchronize()
     clocks.start()
@@ -401,7 +406,8 @@ def run_batched(args):
             "dtype": "f64" if prec == 0 else "f32-pair/f64-state", "data": "synthetic",
             "config": {"workload": f"{len(disks)} planetesimal disks, N log-uniform {args.n_lo}-{args.n_hi} "
                                    f"(seeds 2000+k), all massive, dt=0.5 yr, M=4, one pool",
-                       "sizes": sizes},
+                       "sizes": sizes, "schedule": schedule},
+            "autotune": tune,
             "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
             "serial_fp64_one_at_a_time": {"value": serial_rate, "unit": "sim-steps/s", "steps_each": serial_steps},
             "speedup_vs_serial": pool_rate / serial_rate, "clocks": clk}

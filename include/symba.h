@@ -177,6 +177,58 @@ int symba_pool_evict(symba_pool *pool, int slot);
 
 void symba_pool_free(symba_pool *pool);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Launch schedules and their autotuner.  The pair kick (Sec. 2's trapezoid loop) is a queue   */
+/* of 32 x 32 tiles taken by persistent warps; the encounter groups (Sec. 2: each group is     */
+/* integrated independently) are a queue of groups taken by persistent warps.  How the queues  */
+/* are cut and ordered changes no result -- per-tile partials are reduced in a fixed order and  */
+/* groups touch disjoint bodies -- only the time.                                              */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+  int kick_blocks_per_sm;   /* persistent kick CTAs (4 warps each) per multiprocessor, >= 1 */
+  int kick_tiles_per_item;  /* tiles a warp takes per grab from the tile queue, 1..64 */
+  int rec_blocks_per_sm;    /* recursion CTAs (4 warps, one per SM quadrant) per SM, 1 or 2 */
+  int group_order;          /* 0: groups in label order; 1: longest estimated chain first
+                               (M^k for the deepest shell k the pair's straight-line closest
+                               approach reaches, times the share of the step it stays inside;
+                               up to 16,384 groups per step are ordered, more keep label order) */
+} symba_schedule;
+
+typedef struct {
+  symba_schedule chosen;        /* the schedule in effect when the call returns */
+  double kick_ms;               /* its second-kick time, mean over the repetitions */
+  double recursion_ms;          /* its group-recursion time on the trial step */
+  double kick_ms_before;        /* the same two for the schedule in effect before the call */
+  double recursion_ms_before;
+  int kick_candidates;          /* kick schedules timed */
+  int recursion_candidates;     /* recursion schedules timed */
+  int identical;                /* 1: every recursion trial ended in a bit-identical state */
+  int pad;
+} symba_tune_result;
+
+/* Current schedule of a pool (host struct). */
+int symba_pool_get_schedule(symba_pool *pool, symba_schedule *s);
+
+/* Sets a schedule; SYMBA_E_INVAL for fields outside their ranges (kick_blocks_per_sm above the
+ * kernel's occupancy limit included).  Takes effect at the next step. */
+int symba_pool_set_schedule(symba_pool *pool, const symba_schedule *s);
+
+/* Times candidate schedules on the pool's current systems and keeps the fastest; synchronises.
+ * Kick: every kick_blocks_per_sm up to the occupancy limit x kick_tiles_per_item in
+ * {1, 2, 4, 8, 16}, each timed over reps (>= 1) launches of the second kick, which writes only
+ * per-tile scratch that every step overwrites.  Recursion: rec_blocks_per_sm in {1, 2} x
+ * group_order in {0, 1}, each timed on the same trial step, run from a device copy of the
+ * pool's state (positions, velocities, masses, radii, flags, momenta, statistics) that is put
+ * back before every trial and after the last, so the call leaves every system as it found it.
+ * The copy is allocated for the call (SYMBA_E_NOMEM if it does not fit) and freed.  With no
+ * system admitted it returns SYMBA_OK and leaves the schedule unchanged.  A trial step that
+ * sets an error status does not change the pool's status (it is restored); CUDA failures
+ * return SYMBA_E_CUDA.  out (host) may be NULL. */
+int symba_pool_autotune(symba_pool *pool, int reps, symba_tune_result *out);
+
+/* The same for the pool behind a context. */
+int symba_autotune(symba_ctx *c, int reps, symba_tune_result *out);
+
 /* Human-readable name of a status code. */
 const char *symba_status_string(int status);
 

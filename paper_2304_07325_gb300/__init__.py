@@ -36,7 +36,8 @@ EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "s
             "symba_free", "symba_pool_create", "symba_pool_footprint", "symba_pool_admit",
             "symba_pool_step", "symba_pool_sync", "symba_pool_get_state", "symba_pool_energy",
             "symba_pool_get_stats", "symba_pool_evict", "symba_pool_free", "symba_status_string",
-            "symba_profile_step", "symba_energy_static"]
+            "symba_profile_step", "symba_energy_static", "symba_pool_get_schedule",
+            "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune"]
 SYMBA_NPHASES = 10
 PHASES = ["sun drift + prologue", "kick 1 + encounter check", "kick-1 reduction", "grouping",
           "Kepler drift", "group recursion", "kick 2", "kick-2 reduction", "total momentum",
@@ -54,6 +55,26 @@ class symba_stats(ctypes.Structure):
     _fields_ = [("n_pairs", c_int), ("n_groups", c_int), ("max_depth", c_int), ("status", c_int),
                 ("merges", c_longlong), ("substeps", c_longlong), ("steps", c_longlong),
                 ("max_chain", c_longlong)]
+
+
+class symba_schedule(ctypes.Structure):
+    _fields_ = [("kick_blocks_per_sm", c_int), ("kick_tiles_per_item", c_int),
+                ("rec_blocks_per_sm", c_int), ("group_order", c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class symba_tune_result(ctypes.Structure):
+    _fields_ = [("chosen", symba_schedule), ("kick_ms", c_double), ("recursion_ms", c_double),
+                ("kick_ms_before", c_double), ("recursion_ms_before", c_double),
+                ("kick_candidates", c_int), ("recursion_candidates", c_int), ("identical", c_int),
+                ("pad", c_int)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("chosen", "pad")}
+        d["chosen"] = self.chosen.as_dict()
+        return d
 
 
 class SymbaError(RuntimeError):
@@ -97,6 +118,10 @@ def lib():
             "symba_status_string": (ctypes.c_char_p, [c_int]),
             "symba_profile_step": (c_int, [vp, c_int, dp]),
             "symba_energy_static": (c_int, [c_int, c_int, vp, vp, vp, c_double, c_double, vp, vp]),
+            "symba_pool_get_schedule": (c_int, [vp, POINTER(symba_schedule)]),
+            "symba_pool_set_schedule": (c_int, [vp, POINTER(symba_schedule)]),
+            "symba_pool_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
+            "symba_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -210,6 +235,13 @@ class System:
         _check(lib().symba_get_stats(self._h, byref(s)), "symba_get_stats")
         return s
 
+    def autotune(self, reps: int = 3) -> dict:
+        """Times the launch schedules on this system and keeps the fastest (symba_autotune);
+        the system's state is left as it was."""
+        r = symba_tune_result()
+        _check(lib().symba_autotune(self._h, int(reps), byref(r)), "symba_autotune")
+        return r.as_dict()
+
     def profile_step(self, nsteps: int = 1) -> np.ndarray:
         """Device milliseconds per phase (see PHASES), summed over nsteps steps."""
         out = (c_double * SYMBA_NPHASES)()
@@ -281,6 +313,27 @@ class Pool:
         s = symba_stats()
         _check(lib().symba_pool_get_stats(self._h, int(slot), byref(s)), "symba_pool_get_stats")
         return s
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Times the launch schedules on the admitted systems and keeps the fastest
+        (symba_pool_autotune); every system's state is left as it was."""
+        r = symba_tune_result()
+        _check(lib().symba_pool_autotune(self._h, int(reps), byref(r)), "symba_pool_autotune")
+        return r.as_dict()
+
+    @property
+    def schedule(self) -> dict:
+        s = symba_schedule()
+        _check(lib().symba_pool_get_schedule(self._h, byref(s)), "symba_pool_get_schedule")
+        return s.as_dict()
+
+    @schedule.setter
+    def schedule(self, d: dict) -> None:
+        s = symba_schedule()
+        _check(lib().symba_pool_get_schedule(self._h, byref(s)), "symba_pool_get_schedule")
+        for k, v in d.items():
+            setattr(s, k, int(v))
+        _check(lib().symba_pool_set_schedule(self._h, byref(s)), "symba_pool_set_schedule")
 
     def evict(self, slot: int) -> None:
         _check(lib().symba_pool_evict(self._h, int(slot)), "symba_pool_evict")

@@ -79,6 +79,11 @@ struct symba_pool {
   cudaGraph_t graph = nullptr;
   bool graph_ok = false;
   bool use_graph = true;
+  // launch schedule (symba_schedule): tiles per kick work item (0 = sized from the tile count),
+  // recursion CTAs per SM, group order
+  int seg_override = 0;
+  int rec_bpsm = 1;
+  int group_order = 0;
 };
 
 struct symba_ctx {
@@ -176,7 +181,7 @@ int rebuild(symba_pool *P) {
   P->D.ntiles_total = (int)tiles.size();
   const long long warps = (long long)P->L.trap_blocks * 4;
   long long seg = (long long)tiles.size() / std::max(1LL, warps * 24);
-  P->D.seg_len = (int)std::max(1LL, std::min(8LL, seg));
+  P->D.seg_len = P->seg_override > 0 ? P->seg_override : (int)std::max(1LL, std::min(8LL, seg));
   if (!tiles.empty())
     CK(cudaMemcpyAsync(P->D.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, P->stream));
   // ck tables are filled on the device by the set-up kernel: keep them across uploads
@@ -193,7 +198,8 @@ int rebuild(symba_pool *P) {
   return SYMBA_OK;
 }
 
-void enqueue_step(symba_pool *P) {
+// One step of every system; rec0/rec1 (optional) are recorded around the group recursion.
+void enqueue_step(symba_pool *P, cudaEvent_t rec0 = nullptr, cudaEvent_t rec1 = nullptr) {
   const Dev &D = P->D;
   const long long np = P->npart_hwm;
   launch_prologue(D, P->ndisks, P->stream);
@@ -201,8 +207,11 @@ void enqueue_step(symba_pool *P) {
   launch_trap(D, P->L, 1, P->precision, P->stream);
   launch_reduce(D, np, P->precision, P->stream);
   launch_groups(D, P->ndisks, P->stream);
+  if (P->group_order) launch_order_groups(D, P->stream);
   launch_drift(D, np, P->stream);
+  if (rec0) cudaEventRecord(rec0, P->stream);
   launch_recursion(D, P->L, P->stream);
+  if (rec1) cudaEventRecord(rec1, P->stream);
   if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, P->stream);
   launch_trap(D, P->L, 2, P->precision, P->stream);
   launch_reduce(D, np, P->precision, P->stream);
@@ -240,6 +249,7 @@ int pool_profile(symba_pool *P, int nsteps, double *phase_ms) {
     launch_reduce(D, np, P->precision, s);
     cudaEventRecord(ev[3], s);
     launch_groups(D, P->ndisks, s);
+    if (P->group_order) launch_order_groups(D, s);
     cudaEventRecord(ev[4], s);
     launch_drift(D, np, s);
     cudaEventRecord(ev[5], s);
@@ -319,6 +329,11 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   P->L.sms = prop.multiProcessorCount;
   P->L.trap_blocks = P->L.sms * trap_blocks_per_sm(precision);
   P->L.rec_blocks = P->L.sms * recursion_blocks_per_sm();
+  if (!order_groups_init()) {
+    if (P->own_stream) cudaStreamDestroy(P->stream);
+    delete P;
+    return SYMBA_E_CUDA;
+  }
   const long long n = P->pcap, pc = P->paircap, gs = n / 2 + 1;
   Dev &D = P->D;
   int st = SYMBA_OK;
@@ -347,7 +362,7 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   A(&D.acc, 3 * n);
   A(&D.g_moff, gs); A(&D.g_mcnt, gs); A(&D.g_poff, gs); A(&D.g_pcnt, gs); A(&D.g_cur, gs);
   A(&D.gmem, n); A(&D.rec_items, gs); A(&D.rec_total, 1);
-  A(&D.lcache, (size_t)P->L.rec_blocks * 4 * SYM_PAIR_LC);
+  A(&D.lcache, (size_t)P->L.sms * SYM_REC_BPSM_MAX * 4 * SYM_PAIR_LC);   // any schedule
   A(&P->eacc, 4 * (SA_NDIG + 1)); A(&P->eout, 4);
   if (st != SYMBA_OK) { symba_pool_free(P); return st; }
   if (cudaMemsetAsync(D.blk_disk, 0xFF, sizeof(int) * (n / SYM_TILE + 1), P->stream) != cudaSuccess ||
@@ -552,6 +567,185 @@ int get_stats(symba_pool *P, int d, symba_stats *out) {
   return SYMBA_OK;
 }
 
+
+// --------------------------------------------------------------------------------------------
+// launch schedules and their autotuner
+// --------------------------------------------------------------------------------------------
+void get_schedule(const symba_pool *P, symba_schedule *s) {
+  s->kick_blocks_per_sm = P->L.trap_blocks / P->L.sms;
+  s->kick_tiles_per_item = P->D.seg_len;
+  s->rec_blocks_per_sm = P->rec_bpsm;
+  s->group_order = P->group_order;
+}
+
+bool schedule_valid(const symba_pool *P, const symba_schedule *s) {
+  return s->kick_blocks_per_sm >= 1 && s->kick_blocks_per_sm <= trap_blocks_per_sm(P->precision) &&
+         s->kick_tiles_per_item >= 1 && s->kick_tiles_per_item <= 64 && s->rec_blocks_per_sm >= 1 &&
+         s->rec_blocks_per_sm <= SYM_REC_BPSM_MAX && (s->group_order == 0 || s->group_order == 1);
+}
+
+void apply_schedule(symba_pool *P, const symba_schedule *s) {
+  P->L.trap_blocks = P->L.sms * s->kick_blocks_per_sm;
+  P->seg_override = s->kick_tiles_per_item;
+  P->D.seg_len = s->kick_tiles_per_item;
+  P->rec_bpsm = s->rec_blocks_per_sm;
+  P->L.rec_blocks = P->L.sms * s->rec_blocks_per_sm;
+  P->group_order = s->group_order;
+  invalidate_graph(P);
+}
+
+// The device state a step reads and writes (everything else is per-step scratch or constant).
+struct Span {
+  void *p;
+  size_t bytes;
+};
+std::vector<Span> state_spans(const symba_pool *P) {
+  const Dev &D = P->D;
+  const size_t n = (size_t)P->npart_hwm, nd = (size_t)P->max_disks;
+  std::vector<Span> v;
+  for (double *a : {D.x, D.y, D.z, D.vx, D.vy, D.vz, D.m, D.gm, D.rad, D.rh}) v.push_back({a, n * sizeof(double)});
+  for (int *a : {D.alive, D.gid}) v.push_back({a, n * sizeof(int)});
+  for (float *a : {D.xf, D.yf, D.zf, D.vxf, D.vyf, D.vzf, D.lamf, D.sigf, D.xl, D.yl, D.zl, D.gmf})
+    v.push_back({a, n * sizeof(float)});
+  v.push_back({D.P, 3 * nd * sizeof(double)});
+  v.push_back({D.sacc, nd * 3 * (SA_NDIG + 1) * sizeof(unsigned long long)});
+  v.push_back({D.stat, nd * sizeof(DiskStat)});
+  return v;
+}
+
+size_t span_slot(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
+int copy_spans(const std::vector<Span> &v, char *buf, bool save, cudaStream_t s) {
+  size_t off = 0;
+  for (const Span &sp : v) {
+    if (sp.bytes) {
+      if (save) CK(cudaMemcpyAsync(buf + off, sp.p, sp.bytes, cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemcpyAsync(sp.p, buf + off, sp.bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    off += span_slot(sp.bytes);
+  }
+  return SYMBA_OK;
+}
+
+int pool_autotune(symba_pool *P, int reps, symba_tune_result *out) {
+  if (reps < 1) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  symba_tune_result r;
+  memset(&r, 0, sizeof(r));
+  get_schedule(P, &r.chosen);
+  r.identical = 1;
+  bool any = false;
+  for (int d = 0; d < P->max_disks; ++d) any = any || P->slots[d].active;
+  if (!any || P->ndisks == 0 || P->D.ntiles_total <= 0) {
+    if (out) *out = r;
+    return SYMBA_OK;
+  }
+  CK(cudaStreamSynchronize(P->stream));
+  const symba_schedule before = r.chosen;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  char *snap = nullptr;
+  unsigned long long *hbuf = nullptr;
+  int rc = SYMBA_OK;
+  auto fail = [&](int code) {
+    if (rc == SYMBA_OK) rc = code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) fail(SYMBA_E_CUDA);
+
+  // kick: the second kick (per-tile partials only) under each candidate, mean of reps launches
+  auto time_kick = [&](int kb, int seg) -> double {
+    P->L.trap_blocks = P->L.sms * kb;
+    P->D.seg_len = seg;
+    double tot = 0.0;
+    for (int k = 0; k < reps && rc == SYMBA_OK; ++k) {
+      float ms = 0.f;
+      if (cudaMemsetAsync(P->D.work + 1, 0, sizeof(int), P->stream) != cudaSuccess ||
+          cudaEventRecord(e0, P->stream) != cudaSuccess) { fail(SYMBA_E_CUDA); break; }
+      launch_trap(P->D, P->L, 2, P->precision, P->stream);
+      if (cudaEventRecord(e1, P->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { fail(SYMBA_E_CUDA); break; }
+      tot += ms;
+    }
+    return tot / reps;
+  };
+  symba_schedule best = before;
+  if (rc == SYMBA_OK) {
+    r.kick_ms_before = time_kick(before.kick_blocks_per_sm, before.kick_tiles_per_item);
+    r.kick_ms = r.kick_ms_before;
+    const int kmax = trap_blocks_per_sm(P->precision);
+    for (int kb = 1; kb <= kmax && rc == SYMBA_OK; ++kb) {
+      for (int seg : {1, 2, 4, 8, 16}) {
+        const double ms = time_kick(kb, seg);
+        ++r.kick_candidates;
+        if (rc == SYMBA_OK && ms < r.kick_ms) {
+          r.kick_ms = ms;
+          best.kick_blocks_per_sm = kb;
+          best.kick_tiles_per_item = seg;
+        }
+      }
+    }
+  }
+  apply_schedule(P, rc == SYMBA_OK ? &best : &before);
+
+  // recursion: the same trial step from a copy of the state under each candidate
+  const std::vector<Span> spans = state_spans(P);
+  size_t bytes = 0;
+  for (const Span &sp : spans) bytes += span_slot(sp.bytes);
+  const int cand[4][2] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}};
+  const int nc = 1 + 4;          // the schedule in effect first, then every candidate
+  if (rc == SYMBA_OK && (cudaMalloc(&snap, bytes) != cudaSuccess ||
+                         cudaMalloc(&hbuf, nc * sizeof(unsigned long long)) != cudaSuccess))
+    fail(SYMBA_E_NOMEM);
+  bool saved = false;
+  if (rc == SYMBA_OK && copy_spans(spans, snap, true, P->stream) == SYMBA_OK) saved = true;
+  else fail(SYMBA_E_CUDA);
+  double rec_ms[nc] = {0.0};
+  for (int c = 0; c < nc && rc == SYMBA_OK; ++c) {
+    symba_schedule s = best;
+    if (c > 0) {
+      s.rec_blocks_per_sm = cand[c - 1][0];
+      s.group_order = cand[c - 1][1];
+    }
+    apply_schedule(P, &s);
+    if (copy_spans(spans, snap, false, P->stream) != SYMBA_OK) { fail(SYMBA_E_CUDA); break; }
+    enqueue_step(P, e0, e1);
+    launch_state_hash(P->D, P->npart_hwm, P->ndisks, hbuf + c, P->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) { fail(SYMBA_E_CUDA); break; }
+    rec_ms[c] = ms;
+    if (c > 0) ++r.recursion_candidates;
+  }
+  if (saved && copy_spans(spans, snap, false, P->stream) != SYMBA_OK) fail(SYMBA_E_CUDA);
+  if (rc == SYMBA_OK) {
+    unsigned long long h[nc];
+    if (cudaMemcpyAsync(h, hbuf, sizeof(h), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) {
+      fail(SYMBA_E_CUDA);
+    } else {
+      for (int c = 1; c < nc; ++c) r.identical = r.identical && h[c] == h[0];
+      r.recursion_ms_before = rec_ms[0];
+      r.recursion_ms = rec_ms[0];
+      for (int c = 1; c < nc; ++c) {
+        if (rec_ms[c] < r.recursion_ms) {
+          r.recursion_ms = rec_ms[c];
+          best.rec_blocks_per_sm = cand[c - 1][0];
+          best.group_order = cand[c - 1][1];
+        }
+      }
+      if (best.rec_blocks_per_sm == before.rec_blocks_per_sm && best.group_order == before.group_order)
+        r.recursion_ms = rec_ms[0];
+    }
+  }
+  apply_schedule(P, rc == SYMBA_OK ? &best : &before);
+  if (snap) cudaFree(snap);
+  if (hbuf) cudaFree(hbuf);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc == SYMBA_OK) get_schedule(P, &r.chosen);
+  if (out) *out = r;
+  return rc;
+}
+
 }  // namespace
 
 // ============================================================================================
@@ -617,6 +811,28 @@ int symba_pool_admit(symba_pool *pool, const symba_params *p, int n, int n_massi
 int symba_pool_step(symba_pool *pool, int nsteps) {
   if (!pool) return SYMBA_E_INVAL;
   return pool_step(pool, nsteps);
+}
+
+int symba_pool_get_schedule(symba_pool *pool, symba_schedule *s) {
+  if (!pool || !s) return SYMBA_E_INVAL;
+  get_schedule(pool, s);
+  return SYMBA_OK;
+}
+
+int symba_pool_set_schedule(symba_pool *pool, const symba_schedule *s) {
+  if (!pool || !s || !schedule_valid(pool, s)) return SYMBA_E_INVAL;
+  apply_schedule(pool, s);
+  return SYMBA_OK;
+}
+
+int symba_pool_autotune(symba_pool *pool, int reps, symba_tune_result *out) {
+  if (!pool) return SYMBA_E_INVAL;
+  return pool_autotune(pool, reps, out);
+}
+
+int symba_autotune(symba_ctx *c, int reps, symba_tune_result *out) {
+  if (!c) return SYMBA_E_INVAL;
+  return pool_autotune(c->pool, reps, out);
 }
 
 int symba_pool_sync(symba_pool *pool) {

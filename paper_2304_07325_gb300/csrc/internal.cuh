@@ -16,6 +16,7 @@
 #define SYM_TILE 32
 #define SYM_MAX_LEVELS 32
 #define SYM_PAIR_LC (17 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
+#define SYM_REC_BPSM_MAX 2   // recursion CTAs per SM a schedule may ask for
 #define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
 
 struct DiskDesc {
@@ -560,3 +561,6 @@ void launch_scatter_state(const Dev &D, int d, int n, const double *x, const dou
 void launch_prologue(const Dev &D, int ndisks, cudaStream_t s);
 int trap_blocks_per_sm(int precision);
 int recursion_blocks_per_sm();
+bool order_groups_init();
+void launch_order_groups(const Dev &D, cudaStream_t s);
+void launch_state_hash(const Dev &D, long long np, int ndisks, unsigned long long *h, cudaStream_t s);

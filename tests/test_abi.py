@@ -41,6 +41,8 @@ def test_param_struct_layout_matches_header(built_lib):
     assert abs(p.G - 39.47841760435743) < 1e-14 and p.m0 == 1.0 and p.precision == 0
     assert ctypes.sizeof(sy.symba_params) == 5 * 8 + 6 * 4
     assert ctypes.sizeof(sy.symba_stats) == 4 * 4 + 4 * 8
+    assert ctypes.sizeof(sy.symba_schedule) == 4 * 4
+    assert ctypes.sizeof(sy.symba_tune_result) == 4 * 4 + 4 * 8 + 4 * 4
 
 
 def test_status_strings(built_lib):
@@ -83,3 +85,8 @@ def test_invalid_arguments_are_rejected_before_any_device_call(built_lib):
     assert lib.symba_energy_static(0, 0, None, None, None, 1.0, 1.0, None, None) == sy.SYMBA_E_INVAL
     assert lib.symba_pool_create(C.byref(h), 0, 10, 10, 0, None) == sy.SYMBA_E_INVAL
     assert lib.symba_pool_create(C.byref(h), 1, 10, 10, 7, None) == sy.SYMBA_E_INVAL
+    sched, res = sy.symba_schedule(), sy.symba_tune_result()
+    assert lib.symba_pool_get_schedule(None, C.byref(sched)) == sy.SYMBA_E_INVAL
+    assert lib.symba_pool_set_schedule(None, C.byref(sched)) == sy.SYMBA_E_INVAL
+    assert lib.symba_pool_autotune(None, 1, C.byref(res)) == sy.SYMBA_E_INVAL
+    assert lib.symba_autotune(None, 1, C.byref(res)) == sy.SYMBA_E_INVAL
