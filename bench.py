@@ -36,11 +36,11 @@ FLOPS_PER_PAIR_CHECK = 18
 # sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
 # (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
 DFMA_LATENCY_CYCLES = 64.3
-FP64_INSTR_PER_CHAIN_SUBSTEP = 35.3
+FP64_INSTR_PER_CHAIN_SUBSTEP = 35.5
 # DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
 # trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
-KICK_TRAFFIC_BYTES_N10000 = ((1.84 + 13.59) + (1.44 + 11.96)) / 2 * 1e6
-RECURSION_TRAFFIC_BYTES_N10000 = 1.67e6 + 13.06e3
+KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.63) + (1.43 + 12.09)) / 2 * 1e6
+RECURSION_TRAFFIC_BYTES_N10000 = 1.66e6 + 13.82e3
 
 
 def parse():

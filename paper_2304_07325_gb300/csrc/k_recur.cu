@@ -585,7 +585,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   unsigned long long have = 0ull;
 
   // current level's constants
-  double h, hh, t2, R2, A1, B1, A2, B2, ghs, t3, munh, h15, munh15, munh1875, R2n, R2p;
+  // (h^2, h^3 and 1.5 h serve only the order-3 drift, which reads them from the cache)
+  double h, hh, R2, A1, B1, A2, B2, ghs, munh, munh15, munh1875, R2n, R2p;
   float hf, R2f;
   auto set_level = [&](int jj) {
     double *Lc = lc + LC_N * jj;
@@ -612,10 +613,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       for (int i = 0; i < LC_N; ++i) Lc[i] = v[i];
       have |= 1ull << jj;
     }
-    h = Lc[LC_H]; hh = Lc[LC_HH]; t2 = Lc[LC_T2]; R2 = Lc[LC_R2];
+    h = Lc[LC_H]; hh = Lc[LC_HH]; R2 = Lc[LC_R2];
     A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
     ghs = pb ? -Lc[LC_GHA] : Lc[LC_GHB];
-    t3 = Lc[LC_T3]; munh = Lc[LC_MUNH]; h15 = Lc[LC_H15];
+    munh = Lc[LC_MUNH];
     munh15 = Lc[LC_MUNH15]; munh1875 = Lc[LC_MUNH1875];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
     hf = f32_trunc(h);
@@ -831,6 +832,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       const double s3 = u * bsel(kd3, p, mc1 | mc2);
       const double up = cpy(s3, lane, 0), nhu = cpy(s3, lane, 1), nu6 = cpy(s3, lane, 2);
       // [h/2 up - u/2 | 1.5 h up - u | h up - u/2 | -u h^3/6]
+      // h^2, h^3 and 1.5 h from the level cache (needed only here)
+      const double *Lc = lc + LC_N * j;
+      const double t2 = Lc[LC_T2], t3 = Lc[LC_T3], h15 = Lc[LC_H15];
       const double s4 = fma4(m0, m1, hh, up, nhu, h15, up, -u, h, up, nhu, t3, nu6, -0.0);
       // [f - 1 | f' | g' - 1 | x + h v + (g - h) v]
       const double s5 = fma4(m0, m1, t2, cpy(s4, lane, 0), -0.0, h, cpy(s4, lane, 1), -0.0,
