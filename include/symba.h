@@ -60,6 +60,10 @@ typedef struct {
   int precision;       /* SYMBA_PRECISION_FP64 or SYMBA_PRECISION_MIXED */
   int pair_capacity;   /* level-0 encounter pairs per step; 0 = max(4096, 4 n) */
   int max_substeps;    /* sub-step budget per group and step; 0 = 1 << 22 */
+  double rmin;         /* removal (the paper names no rule; SWIFT-style discard): after the      */
+  double rmax;         /* closing kick of a step, a live body with heliocentric distance below   */
+                       /* rmin (it hit the star) or above rmax (ejected) leaves the system: its  */
+                       /* mass and radii become 0 and it no longer takes part; 0 = no limit     */
 } symba_params;
 
 /* Per-step diagnostics of the last step (summed over a multi-step call where stated). */
@@ -73,6 +77,7 @@ typedef struct {
   long long steps;          /* steps taken since the context was created */
   long long max_chain;      /* most sub-steps of one group in one step during the last call: the
                                dependent chain that bounds the recursion's time */
+  long long removals;       /* bodies removed by rmin / rmax since the context was created */
 } symba_stats;
 
 typedef struct symba_ctx symba_ctx;
@@ -96,7 +101,7 @@ int symba_init(symba_ctx **out, const symba_params *p, int n, int n_massive, con
 /* Enqueues nsteps SyMBA steps E(tau) on the context's stream and returns without waiting.
  * Each step: sun drift tau/2; level-0 check fused into kick tau/2 over the trapezoid; grouping;
  * Kepler drift tau of bodies in no encounter and M-fold recursion of every group; kick tau/2;
- * sun drift tau/2.  Returns SYMBA_OK, SYMBA_E_INVAL (nsteps < 0) or SYMBA_E_CUDA. */
+ * removal by rmin / rmax (when set); sun drift tau/2.  Returns SYMBA_OK, SYMBA_E_INVAL (nsteps < 0) or SYMBA_E_CUDA. */
 int symba_step(symba_ctx *c, int nsteps);
 
 /* Waits for the context's stream; returns the sticky device status (or SYMBA_COLLISION if
@@ -116,7 +121,7 @@ int symba_enc_groups(symba_ctx *c, int *pairs, int *group_of_pair, int cap, int 
                      int *n_groups);
 
 /* Copies the state out: x (n x 3 heliocentric), v (n x 3 barycentric), and optionally m,
- * radius (n) and alive (n ints, 0 for a body merged into another).  Any output may be NULL.
+ * radius (n) and alive (n ints, 0 for a body merged into another or removed).  Any output may be NULL.
  * Synchronises. */
 int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radius, int *alive);
 

@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
 class Params(ctypes.Structure):
     _fields_ = [("dt", c_double), ("shell_ratio", c_double), ("hill_scale", c_double),
                 ("G", c_double), ("m0", c_double), ("M", c_int), ("l", c_int),
-                ("max_depth", c_int), ("noise", c_int)]
+                ("max_depth", c_int), ("noise", c_int), ("rmin", c_double), ("rmax", c_double)]
 
 
 class _Sim(ctypes.Structure):
@@ -47,7 +47,8 @@ class _Sim(ctypes.Structure):
                 ("cap", c_int), ("npairs", c_int), ("ngroups", c_int),
                 ("pairs", POINTER(c_int)), ("group_of_pair", POINTER(c_int)),
                 ("status", c_int), ("max_depth_seen", c_int),
-                ("collisions", c_longlong), ("level_flags", c_longlong * MAX_LEVELS),
+                ("collisions", c_longlong), ("removals", c_longlong),
+                ("level_flags", c_longlong * MAX_LEVELS),
                 ("level_calls", c_longlong * MAX_LEVELS)]
 
 
@@ -94,9 +95,9 @@ def _ip(a):
 
 
 def make_params(dt=0.5, M=4, shell_ratio=2.08, hill_scale=6.5, l=3, G=4.0 * math.pi ** 2, m0=1.0,
-                max_depth=20, noise=0) -> Params:
+                max_depth=20, noise=0, rmin=0.0, rmax=0.0) -> Params:
     return Params(dt=dt, shell_ratio=shell_ratio, hill_scale=hill_scale, G=G, m0=m0, M=M, l=l,
-                  max_depth=max_depth, noise=noise)
+                  max_depth=max_depth, noise=noise, rmin=rmin, rmax=rmax)
 
 
 def fsum(a) -> float:
@@ -210,6 +211,10 @@ class OracleSim:
     @property
     def collisions(self):
         return int(self._s.collisions)
+
+    @property
+    def removals(self):
+        return int(self._s.removals)
 
     @property
     def level_flags(self):

@@ -47,6 +47,9 @@ typedef struct {
                           velocity component a recursion sub-step kicks or drifts is multiplied by
                           1 +- 2^-52 (deterministic pseudo-random sign), to measure how strongly
                           the chaotic close encounters amplify differences at the rounding level */
+  double rmin;         /* removal (reading; the paper names no rule): after the closing kick a  */
+  double rmax;         /* live body with heliocentric r < rmin (the star) or r > rmax (ejected)  */
+                       /* leaves the system; 0 switches a limit off */
 } orc_params;
 
 typedef struct {
@@ -66,6 +69,7 @@ typedef struct {
   int status;          /* worst status of the last step (0 = OK) */
   int max_depth_seen;  /* deepest level entered in the last step */
   long long collisions;            /* mergers (separation < R_i + R_j at a check) in the last step */
+  long long removals;              /* bodies removed by rmin / rmax in the last step */
   long long level_flags[ORC_MAX_LEVELS]; /* pairs flagged at each level, summed over sub-steps */
   long long level_calls[ORC_MAX_LEVELS]; /* sub-steps E_k taken at each level in the last step */
 } orc_sim;
@@ -598,6 +602,27 @@ static void merge_pair(orc_sim *s, int i, int j) {
   s->collisions++;
 }
 
+/* Removal: after the closing kick, a live body whose heliocentric distance is below rmin (it    */
+/* has hit the star) or above rmax (it has been ejected) leaves the system like a body merged    */
+/* away: mass, radii and flag zeroed, so the total momentum of the closing sun drift and of    */
+/* every later sum no longer holds it.  r^2 = (x^2 + y^2) + z^2 against rmin^2 and rmax^2.      */
+static void discard(const orc_params *P, orc_sim *s) {
+  if (!(P->rmin > 0.0) && !(P->rmax > 0.0)) return;
+  const double rmin2 = P->rmin * P->rmin, rmax2 = P->rmax * P->rmax;
+  for (int i = 0; i < s->n; ++i) {
+    if (!s->alive[i]) continue;
+    const double *x = s->x + 3 * i;
+    const double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+    if ((P->rmin > 0.0 && r2 < rmin2) || (P->rmax > 0.0 && r2 > rmax2)) {
+      s->m[i] = 0.0;
+      s->radius[i] = 0.0;
+      s->rhill[i] = 0.0;
+      s->alive[i] = 0;
+      s->removals++;
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Recursive sub-stepping E_k(h) on one component, given its pairs F_{k-1} (sorted):            */
 /*  (i)   F_k = pairs of F_{k-1} flagged at shell k over h;                                     */
@@ -712,6 +737,7 @@ int orc_step(const orc_params *P, orc_sim *s) {
   s->status = ORC_OK;
   s->max_depth_seen = 0;
   s->collisions = 0;
+  s->removals = 0;
   for (int k = 0; k < ORC_MAX_LEVELS; ++k) { s->level_flags[k] = 0; s->level_calls[k] = 0; }
   const int n = s->n;
   const double tau = P->dt, half = 0.5 * tau;
@@ -775,6 +801,7 @@ int orc_step(const orc_params *P, orc_sim *s) {
   if (nF > 0) run_components(&C, 1, tau / (double)P->M, F, (int)nF);
 
   orc_kick_trapezoid(P, s, F, (int)nF, half);
+  discard(P, s);
   sun_drift(P, s, half);
 
   for (int i = 0; i < 3 * n; ++i)

@@ -48,13 +48,13 @@ class symba_params(ctypes.Structure):
     _fields_ = [("dt", c_double), ("shell_ratio", c_double), ("hill_scale", c_double),
                 ("G", c_double), ("m0", c_double), ("M", c_int), ("l", c_int),
                 ("max_depth", c_int), ("precision", c_int), ("pair_capacity", c_int),
-                ("max_substeps", c_int)]
+                ("max_substeps", c_int), ("rmin", c_double), ("rmax", c_double)]
 
 
 class symba_stats(ctypes.Structure):
     _fields_ = [("n_pairs", c_int), ("n_groups", c_int), ("max_depth", c_int), ("status", c_int),
                 ("merges", c_longlong), ("substeps", c_longlong), ("steps", c_longlong),
-                ("max_chain", c_longlong)]
+                ("max_chain", c_longlong), ("removals", c_longlong)]
 
 
 class symba_schedule(ctypes.Structure):

@@ -84,6 +84,7 @@ struct symba_pool {
   int seg_override = 0;
   int rec_bpsm = 1;
   int group_order = 0;
+  bool any_discard = false;   // some system has a removal distance: the step runs k_discard
 };
 
 struct symba_ctx {
@@ -156,6 +157,7 @@ int rebuild(symba_pool *P) {
     phw = std::max(phw, (long long)s.off + (long long)s.nb * SYM_TILE);
   }
   std::vector<DiskDesc> descs(P->max_disks);
+  bool any_discard = false;
   for (int d = 0; d < P->max_disks; ++d) {
     Slot &s = P->slots[d];
     DiskDesc &dd = descs[d];
@@ -171,12 +173,16 @@ int rebuild(symba_pool *P) {
     dd.max_substeps = s.p.max_substeps > 0 ? s.p.max_substeps : (1 << 22);
     dd.dt = s.p.dt; dd.shell_ratio = s.p.shell_ratio; dd.hill_scale = s.p.hill_scale;
     dd.G = s.p.G; dd.m0 = s.p.m0;
+    dd.rmin2 = s.p.rmin > 0.0 ? s.p.rmin * s.p.rmin : 0.0;
+    dd.rmax2 = s.p.rmax > 0.0 ? s.p.rmax * s.p.rmax : 0.0;
+    any_discard = any_discard || dd.rmin2 > 0.0 || dd.rmax2 > 0.0;
     const int b0 = s.off / SYM_TILE;
     for (int I = 0; I < s.nbm; ++I)
       for (int J = I; J < s.nb; ++J) tiles.push_back(make_int4(d, b0 + I, b0 + J, 0));
   }
   P->ndisks = hw;
   P->npart_hwm = phw;
+  P->any_discard = any_discard;
   P->D.ndisks = hw;
   P->D.ntiles_total = (int)tiles.size();
   const long long warps = (long long)P->L.trap_blocks * 4;
@@ -215,6 +221,7 @@ void enqueue_step(symba_pool *P, cudaEvent_t rec0 = nullptr, cudaEvent_t rec1 = 
   if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, P->stream);
   launch_trap(D, P->L, 2, P->precision, P->stream);
   launch_reduce(D, np, P->precision, P->stream);
+  if (P->any_discard) launch_discard(D, np, P->stream);
   launch_momentum(D, P->ndisks, P->stream);
   launch_sundrift(D, np, 0, P->stream);
 }
@@ -259,6 +266,7 @@ int pool_profile(symba_pool *P, int nsteps, double *phase_ms) {
     launch_trap(D, P->L, 2, P->precision, s);
     cudaEventRecord(ev[7], s);
     launch_reduce(D, np, P->precision, s);
+    if (P->any_discard) launch_discard(D, np, s);
     cudaEventRecord(ev[8], s);
     launch_momentum(D, P->ndisks, s);
     cudaEventRecord(ev[9], s);
@@ -386,7 +394,8 @@ int pool_admit(symba_pool *P, const symba_params *p, int n, int nm, const double
                const double *m, const double *radius, const double *rhill, int *slot) {
   if (!P || !p || !x || !v || !m || !radius || n < 1 || nm < 0 || nm > n) return SYMBA_E_INVAL;
   if (p->dt == 0.0 || !(p->shell_ratio > 1.0) || p->M < 1 || p->l < 1 || p->max_depth < 1 ||
-      !(p->m0 > 0.0) || !(p->hill_scale >= 0.0))
+      !(p->m0 > 0.0) || !(p->hill_scale >= 0.0) || !(p->rmin >= 0.0) || !(p->rmax >= 0.0) ||
+      !std::isfinite(p->rmin) || !std::isfinite(p->rmax) || (p->rmax > 0.0 && p->rmin >= p->rmax))
     return SYMBA_E_INVAL;
   CK(cudaSetDevice(P->device));
   int d = -1;
@@ -563,6 +572,7 @@ int get_stats(symba_pool *P, int d, symba_stats *out) {
   out->merges = (long long)st.merges;
   out->substeps = (long long)st.substeps;
   out->max_chain = (long long)st.max_chain;
+  out->removals = (long long)st.removals;
   out->steps = 0;
   return SYMBA_OK;
 }

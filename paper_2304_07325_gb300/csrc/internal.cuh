@@ -26,6 +26,7 @@ struct DiskDesc {
   int group_base;               // this system's slice of the group slots (= off / 2)
   int active, M, l, max_depth, max_substeps, pad0;
   double dt, shell_ratio, hill_scale, G, m0;
+  double rmin2, rmax2;          // squared removal distances (0 = no limit)
   double ck[SYM_MAX_LEVELS + 2];    // c_k = c_{k-1} / shell_ratio, c_0 = 1 (R_k = R_0 c_k)
   double ck2[SYM_MAX_LEVELS + 2];   // c_k^2
   double invdc[SYM_MAX_LEVELS + 2]; // 1 / (c_k - c_{k+1})
@@ -35,6 +36,7 @@ struct DiskStat {               // mutable per-system counters (device)
   int npairs, ngroups, status, max_depth;
   unsigned long long merges, substeps, merges_reported;
   unsigned long long max_chain;   // most sub-steps of one group in one step
+  unsigned long long removals;    // bodies removed by rmin / rmax
 };
 
 struct Dev {
@@ -559,6 +561,7 @@ void launch_gather_state(const Dev &D, int d, int n, double *x, double *v, doubl
 void launch_scatter_state(const Dev &D, int d, int n, const double *x, const double *v,
                           cudaStream_t s);
 void launch_prologue(const Dev &D, int ndisks, cudaStream_t s);
+void launch_discard(const Dev &D, long long npart, cudaStream_t s);
 int trap_blocks_per_sm(int precision);
 int recursion_blocks_per_sm();
 bool order_groups_init();

@@ -25,9 +25,40 @@ __global__ void k_setup_disk(Dev D, int d) {
   st->substeps = 0;
   st->max_chain = 0;
   st->merges_reported = 0;
+  st->removals = 0;
 }
 
 void launch_setup_disk(const Dev &D, int d, cudaStream_t s) { k_setup_disk<<<1, 32, 0, s>>>(D, d); }
+
+// --------------------------------------------------------------------------------------------
+// removal after the closing kick: a live body with r^2 = (x^2 + y^2) + z^2 (each operation
+// rounded once) below rmin^2 or above rmax^2 leaves the system the way a body merged away does
+// (mass, G m, radius and Hill radius 0, flag 0), before the total momentum of the closing sun
+// drift is summed
+// --------------------------------------------------------------------------------------------
+__global__ void k_discard(Dev D, long long npart) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npart;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int d = D.blk_disk[p >> 5];
+    if (d < 0) continue;
+    const DiskDesc &dd = D.disks[d];
+    if (!dd.active || !D.alive[p] || (dd.rmin2 <= 0.0 && dd.rmax2 <= 0.0)) continue;
+    const double x = D.x[p], y = D.y[p], z = D.z[p];
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+    if ((dd.rmin2 > 0.0 && r2 < dd.rmin2) || (dd.rmax2 > 0.0 && r2 > dd.rmax2)) {
+      D.m[p] = 0.0;
+      D.gm[p] = 0.0;
+      D.rad[p] = 0.0;
+      D.rh[p] = 0.0;
+      D.alive[p] = 0;
+      atomicAdd(&D.stat[d].removals, 1ull);
+    }
+  }
+}
+
+void launch_discard(const Dev &D, long long npart, cudaStream_t s) {
+  if (npart > 0) k_discard<<<(int)std::min((npart + 255) / 256, 4096LL), 256, 0, s>>>(D, npart);
+}
 
 // --------------------------------------------------------------------------------------------
 // initial upload: heliocentric -> barycentric velocities with exact sums

@@ -115,6 +115,7 @@ __global__ void k_state_hash(Dev D, long long np, int ndisks, unsigned long long
       acc += mix64((unsigned long long)(unsigned)s.npairs ^ mix64(0x5000000000000002ull + 8ull * d));
       acc += mix64((unsigned long long)(unsigned)s.ngroups ^ mix64(0x5000000000000003ull + 8ull * d));
       acc += mix64((unsigned long long)(unsigned)s.status ^ mix64(0x5000000000000004ull + 8ull * d));
+      acc += mix64((unsigned long long)s.removals ^ mix64(0x5000000000000005ull + 8ull * d));
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -221,6 +221,54 @@ def test_kepler_drift_short_intervals_unbiased(orc, h, steps):
     assert np.linalg.norm(x - xr) / R < 1e-13
 
 
+@pytest.mark.parametrize("direction", ["outbound", "inbound"])
+def test_removal_at_the_closed_form_crossing_step(orc, direction):
+    """A lone massless particle on a hyperbolic orbit (e = 1.5, q = 2 AU) moves on the exact
+    two-body flow.  With rmax halfway between its closed-form distances at the ends of steps 4
+    and 5 on the way out (rmin likewise on the way in), it must stay through step 4 and leave
+    the system at the end of step 5, and stay removed."""
+    mu, tau, e, q = G, 0.5, 1.5, 2.0
+    xp = np.array([q, 0.0, 0.0])
+    vp = np.array([0.0, math.sqrt(mu * (e + 1.0) / q), 0.0])
+    t0 = 0.1 if direction == "outbound" else -6.0
+    x0, v0 = closed_form_hyperbolic(xp, vp, mu, t0)
+    r = [math.sqrt(p @ p) for p in (closed_form_hyperbolic(xp, vp, mu, t0 + k * tau)[0] for k in range(7))]
+    lim = 0.5 * (r[4] + r[5])
+    if direction == "outbound":
+        assert r[4] < lim < r[5]
+        params = orc.make_params(rmax=lim)
+    else:
+        assert r[4] > lim > r[5] and min(r[:5]) > lim
+        params = orc.make_params(rmin=lim)
+    sim = orc.OracleSim([x0], [v0], [0.0], [0.0], n_massive=0, params=params)
+    for _ in range(4):
+        sim.step(1)
+        assert sim.alive[0] == 1 and sim.removals == 0
+    sim.step(1)
+    assert sim.alive[0] == 0 and sim.removals == 1
+    x_removed = sim.x.copy()
+    sim.step(2)
+    assert sim.alive[0] == 0 and sim.removals == 0 and np.array_equal(sim.x, x_removed)
+
+
+def test_removing_a_massless_particle_changes_no_other_body(orc):
+    """A field particle on a circular orbit at 150 AU with rmax = 100 AU leaves at the end of the
+    first step; having no mass, it never acted on the 40 bodies of the disk, whose states must
+    equal, bit for bit, those of the same disk integrated without it."""
+    d = disk.planetesimal_disk(40, 77)
+    x = np.vstack([d.x, [[150.0, 0.0, 0.0]]])
+    v = np.vstack([d.v, [[0.0, math.sqrt(G / 150.0), 0.0]]])
+    m, rad = np.append(d.m, 0.0), np.append(d.radius, 0.0)
+    a = orc.OracleSim(x, v, m, rad, n_massive=40, params=orc.make_params(rmax=100.0))
+    b = orc.OracleSim(d.x, d.v, d.m, d.radius, params=orc.make_params(rmax=100.0), rhill=a.rhill[:40])
+    a.step(1)
+    b.step(1)
+    assert a.alive[40] == 0 and a.removals == 1 and a.alive[:40].all() and b.removals == 0
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.x[:40], b.x) and np.array_equal(a.v[:40], b.v)
+
+
 def test_kepler_drift_zero_dt_is_identity(orc):
     rng = np.random.default_rng(2)
     x, v = _random_orbit(rng, 0.2, G, 3.0)
