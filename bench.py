@@ -40,6 +40,9 @@ FP64_INSTR_PER_CHAIN_SUBSTEP = 35.5
 # DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
 # trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
 KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.63) + (1.43 + 12.09)) / 2 * 1e6
+# FP64 pipe of the kick kernels busy (ncu sm__pipe_fp64_cycles_active over active cycles, kick 1
+# and kick 2 at N = 10,000, FP64): the issue-side fraction of the FP64 peak
+KICK_FP64_PIPE_ACTIVE_N10000 = (0.883 + 0.887) / 2
 RECURSION_TRAFFIC_BYTES_N10000 = 1.66e6 + 13.82e3
 
 
@@ -318,7 +321,10 @@ def run_ours(args):
                          "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                          "frac": kick_achieved / FP64_PEAK_TFLOPS_NOMINAL,
                          "traffic": KICK_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
-                         "ms_per_launch": kick_ms, "peak_source": peak_note}
+                         "ms_per_launch": kick_ms, "peak_source": peak_note,
+                         "fp64_pipe_active": KICK_FP64_PIPE_ACTIVE_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
+                         "fp64_pipe_active_source": "ncu sm__pipe_fp64_cycles_active (kick 1, kick 2), "
+                                                    "profiles/k_trap_fp64_disk_N10000.md"}
         phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
         cb = None
         if not args.no_cpu_baseline and world == 1:
