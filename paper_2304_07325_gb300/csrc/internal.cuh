@@ -96,7 +96,7 @@ __device__ __forceinline__ int find_disk(const int *blk_disk, int p) { return bl
 // r^-3 for the pair kick: seed 1/sqrt(r2) from the top 23 mantissa bits of r2 with one MUFU
 // rsqrt (exponent re-biased with integer operations, so no FP64 conversion is issued), then the
 // third-order correction r^-3 = y0^3 (1 - e)^{-3/2} ~ y0^3 (1 + 3/2 e + 15/8 e^2),
-// e = 1 - r2 y0^2 (|e| < 2^-19, truncation < 2^-57): 6 FP64 instructions.  Values of r2 outside
+// e = 1 - r2 y0^2 (|e| < 2^-19, truncation < 2^-57): 5 FP64 instructions.  Values of r2 outside
 // the normal FP32 range take the library path.
 __device__ __forceinline__ double rinv3(double r2) {
   const int hi = __double2hiint(r2);
@@ -110,7 +110,14 @@ __device__ __forceinline__ double rinv3(double r2) {
     const unsigned yb = __float_as_uint(y0f);
     const int ye = (int)((yb >> 23) & 0xFF) + 896;
     const double y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
-    const double t = y0 * y0;          // exact: y0 has 24 significant bits
+    // t = y0^2, exact (24 significant bits squared), built from the integer square of the
+    // mantissa so that no FP64 instruction is spent on it
+    const unsigned long long my = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u);
+    const unsigned long long sq = my * my;                 // in [2^46, 2^48)
+    const int top = (int)(sq >> 47);
+    const long long te = 2 * (ye - 1023) + top + 1023;
+    const double t = __longlong_as_double((long long)(((unsigned long long)te << 52) |
+                                                      ((sq << (6 - top)) & 0xFFFFFFFFFFFFFull)));
     const double y03 = t * y0;
     const double e = fma(-r2, t, 1.0);
     const double p = fma(e, 1.875, 1.5);
