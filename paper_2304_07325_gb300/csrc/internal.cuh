@@ -469,11 +469,15 @@ __device__ inline int kepler_drift(double mu, double dt, double &x, double &y, d
 __device__ __forceinline__ float f32_trunc(double a) {
   // FP64 -> FP32 by bit manipulation (truncation; no FP64-pipe conversion); for |a| in the normal
   // FP32 range, relative error < 2^-23, which the order decision below leaves margin for
-  const long long b = __double_as_longlong(a);
-  const int e = (int)((b >> 52) & 0x7FF) - 896;
-  if (e <= 0) return 0.0f;
-  if (e >= 255) return __int_as_float(((int)(b >> 32) & 0x80000000) | 0x7F800000);
-  return __int_as_float(((int)(b >> 32) & 0x80000000) | (e << 23) | (int)((b >> 29) & 0x7FFFFF));
+  // (|a| bits << 3 | the next 3 mantissa bits) carries the exponent's low 9 bits over the FP32
+  // exponent field; adding 2^30 re-biases it (1023 - 127 = 896 = 512 + 384) for every exponent
+  // of the normal FP32 range.  Below it: +0; above it (and Inf, NaN): Inf with the sign.
+  const unsigned hi = (unsigned)__double2hiint(a), lo = (unsigned)__double2loint(a);
+  const unsigned mag = hi & 0x7FFFFFFFu;
+  unsigned r = __funnelshift_l(lo, mag, 3) + 0x40000000u;
+  r = mag >= 0x47F00000u ? 0x7F800000u : r;
+  r |= hi & 0x80000000u;
+  return __uint_as_float(mag < 0x38100000u ? 0u : r);
 }
 
 __device__ __forceinline__ bool drift_series(double mu, double t, double &x, double &y, double &z,
