@@ -651,8 +651,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   auto forces = [&]() {
     fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
     const bool inner = lt_nn(r2, R2);        // w_j = g_j inside R_j, 1 - g_{j-1} outside
-    const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
-    const double g = fz ? 0.0 : ghs;
+    // the weight's level constants, chosen by bit selects (no branch): A, B from shell j
+    // (inside R_j) or j - 1, zero with g when the weight vanishes
+    const unsigned m_in = inner ? 0xffffffffu : 0u, m_fz = fz ? 0xffffffffu : 0u;
+    const double A = bsel(0.0, bsel(A1, A2, m_in), m_fz), B = bsel(0.0, bsel(B1, B2, m_in), m_fz);
+    const double g = bsel(0.0, ghs, m_fz);
+    const long long s_out = inner ? 0ll : (long long)0x8000000000000000ull;   // sign of x^4
     if (rcache && c_lvl == j - 1 && c_inner && !inner && !fz) {
       // entering level j at the positions of the last level-(j-1) force, with the pair between
       // R_j and R_{j-1}: the weights telescope, w_j = 1 - g_{j-1}(r) = 1 - w_{j-1} (the same
@@ -672,7 +676,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
     // [+-x^4 | x^2 qa + qb | 1/r^3]  (the sign of x^4 picks f or 1 - f)
-    const double x2s = inner ? x2 : neg(x2);
+    const double x2s = flip(x2, s_out);
     const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1);
     const double ri3 = rcache ? c_ri3 : cpy(s2, lane, 2);
@@ -682,7 +686,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     // no clamp of x to [0, 1]: outside [R_{j+1}, R_{j-1}) the weight is zero (fz, x = 0 above),
     // inside x leaves [0, 1] only by rounding, where f_3 (flat at both ends) differs from 0 or
     // 1 by O(x^4) or O((x - 1)^2)
-    const double w = fma(x4s, q, inner ? -0.0 : 1.0);
+    const double w = fma(x4s, q, bsel(-0.0, 1.0, m_in));
     hc = w * (ri3 * g);
     c_f = w;
     c_lvl = j;
@@ -693,8 +697,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   auto forces_nb = [&]() {
     fz = lt_nn(r2, R2n) || !lt_nn(r2, R2p);
     const bool inner = lt_nn(r2, R2);
-    const double A = fz ? 0.0 : (inner ? A1 : A2), B = fz ? 0.0 : (inner ? B1 : B2);
-    const double g = fz ? 0.0 : ghs;
+    // the weight's level constants, chosen by bit selects (no branch): A, B from shell j
+    // (inside R_j) or j - 1, zero with g when the weight vanishes
+    const unsigned m_in = inner ? 0xffffffffu : 0u, m_fz = fz ? 0xffffffffu : 0u;
+    const double A = bsel(0.0, bsel(A1, A2, m_in), m_fz), B = bsel(0.0, bsel(B1, B2, m_in), m_fz);
+    const double g = bsel(0.0, ghs, m_fz);
+    const long long s_out = inner ? 0ll : (long long)0x8000000000000000ull;   // sign of x^4
     bool ok;
     const double ri = rsq_nb(r2, r2e, ok);
     f_ok = __all_sync(FULL, ok);
@@ -702,10 +710,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double s1 = stage1(xw, ri);
     const double x2 = cpy(s1, lane, 0), qa = cpy(s1, lane, 1), qb = cpy(s1, lane, 2);
     const double ri2 = cpy(s1, lane, 3);
-    const double x2s = inner ? x2 : neg(x2);
+    const double x2s = flip(x2, s_out);
     const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1), ri3 = cpy(s2, lane, 2);
-    const double w = fma(x4s, q, inner ? -0.0 : 1.0);
+    const double w = fma(x4s, q, bsel(-0.0, 1.0, m_in));
     hc = w * (ri3 * g);
     c_ri = ri;
     c_ri3 = ri3;
