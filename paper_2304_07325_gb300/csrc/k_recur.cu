@@ -615,7 +615,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     }
     h = Lc[LC_H]; hh = Lc[LC_HH]; R2 = Lc[LC_R2];
     A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
-    ghs = pb ? -Lc[LC_GHA] : Lc[LC_GHB];
+    ghs = flip(Lc[pb ? LC_GHA : LC_GHB], sgn_b);       // -G m_a h/2 on body b, G m_b h/2 on a
     munh = Lc[LC_MUNH];
     munh15 = Lc[LC_MUNH15]; munh1875 = Lc[LC_MUNH1875];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
@@ -679,7 +679,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const double x2s = flip(x2, s_out);
     const double s2 = stage2(x2s, x2, qa, qb, ri2, ri);
     const double x4s = cpy(s2, lane, 0), q = cpy(s2, lane, 1);
-    const double ri3 = rcache ? c_ri3 : cpy(s2, lane, 2);
+    const double ri3 = bsel(c_ri3, cpy(s2, lane, 2), rcache ? 0xffffffffu : 0u);
     c_ri = ri;
     c_ri3 = ri3;
     rcache = true;
@@ -735,7 +735,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // FP64 predicate would flag; check_exact() is the FP64 predicate.
   auto far_apart = [&](double U) -> bool {
     const float uf = f32_trunc(U), uo = __shfl_xor_sync(FULL, uf, 4);
-    const float dvf = pb ? uf - uo : uo - uf, av = fabsf(uf) + fabsf(uo);
+    // u_b - u_a on both bodies' lanes (only its square is used)
+    const float dvf = __uint_as_float(__float_as_uint(uf - uo) ^ (pb ? 0u : 0x80000000u));
+    const float av = fabsf(uf) + fabsf(uo);
     const float p0 = dvf * dvf;
     const float s2 = (__shfl_sync(FULL, p0, base) + __shfl_sync(FULL, p0, base + 1)) +
                      __shfl_sync(FULL, p0, base + 2);
