@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--n-hi", type=int, default=10000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--steps-cap", type=int, default=40)
+    ap.add_argument("--second-n", type=int, default=5000,
+                    help="single mode: also time this disk size (0 = off), reported under 'second'")
+    ap.add_argument("--second-seed", type=int, default=1001)
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched mode: keep the default launch schedule instead of autotuning it")
     return ap.parse_args()
@@ -202,6 +205,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_second_disk(sy, disk, n, seed, steps, warmup, stream, flush):
+    """The same device-timed measurement on a second disk size (the other benchmark size), one
+    GPU: value and steps/s over `steps` steps after `warmup`, L2 flushed between steps."""
+    import torch
+    d = disk.planetesimal_disk(n, seed)
+    P = n * (n - 1) // 2
+    s = sy.System(d.x, d.v, d.m, d.radius, stream=stream)
+    s.profile_step(max(1, warmup))
+    if s.sync() < 0:
+        raise RuntimeError("second disk: warm-up failed")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    chain = []
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        ph = s.profile_step(1)
+        ends[k].record(stream)
+        st = s.stats()
+        if st.max_chain > 0:
+            chain.append(1e3 * ph[5] / st.max_chain)
+    torch.cuda.synchronize()
+    if s.sync() < 0:
+        raise RuntimeError("second disk: timed steps failed")
+    ms = [starts[k].elapsed_time(ends[k]) for k in range(steps)]
+    t = sum(ms) / 1e3
+    s.close()
+    return {"n": n, "seed": seed, "pairs_per_kick": P, "steps": steps, "warmup": warmup,
+            "value": 2.0 * P * steps / t, "unit": "pair-interactions/s", "steps_per_s": steps / t,
+            "ms_per_step": 1e3 * t / steps, "p50_step_ms": statistics.median(ms),
+            "p99_step_ms": float(np.percentile(ms, 99)),
+            "us_per_chain_substep_median": statistics.median(chain) if chain else None}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -326,6 +365,10 @@ def run_ours(args):
                          "fp64_pipe_active_source": "ncu sm__pipe_fp64_cycles_active (kick 1, kick 2), "
                                                     "profiles/k_trap_fp64_disk_N10000.md"}
         phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
+        second = None
+        if args.second_n > 0 and world == 1 and args.n_field == 0 and prec == 0:
+            second = time_second_disk(sy, disk, args.second_n, args.second_seed, min(args.steps, 50),
+                                      args.warmup, stream, flush)
         cb = None
         if not args.no_cpu_baseline and world == 1:
             cb, _, _ = cpu_baseline(args, d, P, args.cpu_budget_s)
@@ -349,7 +392,7 @@ def run_ours(args):
                         "h2d_bytes_per_step": 2 * 8 * 3 * ntot, "d2h_bytes_per_step": 2 * 8 * 3 * ntot,
                         "steps": ne},
                 "gpu_launches": args.steps * 12,
-                "clocks": clk, "wall_s": wall}
+                "clocks": clk, "wall_s": wall, "second": second}
         print(json.dumps(line), flush=True)
     sysm.close()
     if world > 1:
