@@ -416,8 +416,8 @@ def run_batched(args):
     prec = sy.SYMBA_PRECISION_MIXED if args.precision == "mixed" else sy.SYMBA_PRECISION_FP64
     tiles = sum(tiles_for(d.n, d.n_massive) for d in disks)
     pool = sy.Pool(len(disks), sum(d.n for d in disks) + 32 * len(disks), tiles, prec)
-    for d in disks:
-        pool.admit(d.x, d.v, d.m, d.radius)
+    slots = [pool.admit(d.x, d.v, d.m, d.radius) for d in disks]
+    E0 = [pool.energy(s)[0] for s in slots]
     pool.step(args.warmup)
     pool.sync()
     # launch schedules timed on this pool (state left as it was), the fastest kept
@@ -434,18 +434,27 @@ def run_batched(args):
         step_ms.append(1e3 * (time.perf_counter() - t0))
     clk = clocks.stop()
     t_pool = sum(step_ms) / 1e3
+    # energy error per disk; mergers (inelastic) change the energy, so disks that had one are
+    # reported apart from the integration error of the others
+    dE = [abs((pool.energy(s)[0] - e0) / e0) for s, e0 in zip(slots, E0)]
+    merged = [pool.stats(s).merges > 0 for s in slots]
+    dE_clean = [e for e, mg in zip(dE, merged) if not mg]
     pool.close()
     # the same disks one context (one launch sequence) at a time, FP64
     serial_steps = max(1, min(args.steps, 5))
     t_serial = 0.0
+    dE_serial = []
     for d in disks:
         s1 = sy.System(d.x, d.v, d.m, d.radius)
+        e0 = s1.energy()[0]
         s1.step(1)
         s1.sync()
         t0 = time.perf_counter()
         s1.step(serial_steps)
         s1.sync()
         t_serial += time.perf_counter() - t0
+        if s1.stats().merges == 0:
+            dE_serial.append(abs((s1.energy()[0] - e0) / e0))
         s1.close()
     pool_rate = len(disks) * args.steps / t_pool
     serial_rate = len(disks) * serial_steps / t_serial
@@ -458,7 +467,15 @@ def run_batched(args):
                        "sizes": sizes, "schedule": schedule},
             "autotune": tune,
             "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
-            "serial_fp64_one_at_a_time": {"value": serial_rate, "unit": "sim-steps/s", "steps_each": serial_steps},
+            "energy_error": {"max_no_merger": max(dE_clean) if dE_clean else None,
+                             "median_no_merger": statistics.median(dE_clean) if dE_clean else None,
+                             "disks_no_merger": len(dE_clean), "max_all": max(dE),
+                             "steps": args.warmup + args.steps,
+                             "what": "|E - E0| / |E0| per disk after the pool's steps; disks with a "
+                                     "merger (inelastic, energy not conserved) counted apart"},
+            "serial_fp64_one_at_a_time": {"value": serial_rate, "unit": "sim-steps/s", "steps_each": serial_steps,
+                                          "energy_error_max_no_merger": max(dE_serial) if dE_serial else None,
+                                          "energy_steps": 1 + serial_steps},
             "speedup_vs_serial": pool_rate / serial_rate, "clocks": clk}
     print(json.dumps(line), flush=True)
 
