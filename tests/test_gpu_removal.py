@@ -92,3 +92,27 @@ def test_without_limits_no_body_leaves(sy):
     assert s.sync() >= 0
     assert s.stats().removals == 0 and s.get_state()[4].all()
     s.close()
+
+
+def test_removal_limits_are_per_system_in_a_pool(sy):
+    """Two systems in one pool with different limits (and one without): each removes exactly what
+    it removes alone, bit for bit, so the limits travel with the system."""
+    x, v, m, rad, nm = _system()
+    specs = [dict(rmin=2.0, rmax=30.0), dict(rmax=45.0), dict()]
+    alone = []
+    for lim in specs:
+        s = sy.System(x, v, m, rad, n_massive=nm, params=sy.default_params(**lim))
+        s.step(2)
+        assert s.sync() >= 0
+        alone.append((s.get_state(), s.stats().removals))
+        s.close()
+    pool = sy.Pool(4, 4 * (len(m) + 64), 4 * ((len(m) + 31) // 32) ** 2)
+    slots = [pool.admit(x, v, m, rad, n_massive=nm, params=sy.default_params(**lim)) for lim in specs]
+    pool.step(2)
+    assert pool.sync() >= 0
+    for slot, ((xa, va, ma, ra, aa), removed) in zip(slots, alone):
+        xp, vp, mp, rp, ap = pool.get_state(slot)
+        assert np.array_equal(xp, xa) and np.array_equal(vp, va) and np.array_equal(ap, aa)
+        assert pool.stats(slot).removals == removed
+    assert [r for _, r in alone] == [4, 1, 0]
+    pool.close()
