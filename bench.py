@@ -283,7 +283,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     t_wall0 = time.perf_counter()
-    depth_max, substeps = 0, 0
+    depth_max, substeps, pair_substeps = 0, 0, 0
     chain_us_list = []                         # recursion time per sub-step of the longest chain
     chain_max = 0
     for k in range(args.steps):
@@ -296,6 +296,7 @@ def run_ours(args):
         s = sysm.stats()
         depth_max = max(depth_max, s.max_depth)
         substeps += s.substeps
+        pair_substeps += s.pair_substeps
         chain_max = max(chain_max, s.max_chain)
         if s.max_chain > 0:
             chain_us_list.append(1e3 * ph[5] / s.max_chain)
@@ -386,6 +387,7 @@ def run_ours(args):
                 "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "phase_ms_per_step": phases, "max_depth": depth_max,
                 "substeps_per_step": substeps / args.steps, "longest_chain_substeps": chain_max,
+                "pair_path_share_of_substeps": pair_substeps / substeps if substeps else None,
                 "us_per_chain_substep_median": statistics.median(chain_us_list) if chain_us_list else None,
                 "roofline": roofline, "roofline_kick": roofline_kick, "cpu_baseline": cb,
                 "e2e": {"value": e2e_value, "unit": "pair-interactions/s",

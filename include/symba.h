@@ -78,6 +78,8 @@ typedef struct {
   long long max_chain;      /* most sub-steps of one group in one step during the last call: the
                                dependent chain that bounds the recursion's time */
   long long removals;       /* bodies removed by rmin / rmax since the context was created */
+  long long pair_substeps;  /* of the sub-steps of the last call, those the single-pair path took
+                               (a pair alone in F_{k-1}, its two bodies packed across the warp) */
 } symba_stats;
 
 typedef struct symba_ctx symba_ctx;

@@ -54,7 +54,7 @@ class symba_params(ctypes.Structure):
 class symba_stats(ctypes.Structure):
     _fields_ = [("n_pairs", c_int), ("n_groups", c_int), ("max_depth", c_int), ("status", c_int),
                 ("merges", c_longlong), ("substeps", c_longlong), ("steps", c_longlong),
-                ("max_chain", c_longlong), ("removals", c_longlong)]
+                ("max_chain", c_longlong), ("removals", c_longlong), ("pair_substeps", c_longlong)]
 
 
 class symba_schedule(ctypes.Structure):

@@ -231,6 +231,7 @@ __global__ void k_reset_call(DiskStat *st, int nd) {
     st[d].max_depth = 0;
     st[d].substeps = 0;
     st[d].max_chain = 0;
+    st[d].pair_substeps = 0;
   }
 }
 
@@ -572,6 +573,7 @@ int get_stats(symba_pool *P, int d, symba_stats *out) {
   out->merges = (long long)st.merges;
   out->substeps = (long long)st.substeps;
   out->max_chain = (long long)st.max_chain;
+  out->pair_substeps = (long long)st.pair_substeps;
   out->removals = (long long)st.removals;
   out->steps = 0;
   return SYMBA_OK;

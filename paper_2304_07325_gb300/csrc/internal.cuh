@@ -37,6 +37,7 @@ struct DiskStat {               // mutable per-system counters (device)
   unsigned long long merges, substeps, merges_reported;
   unsigned long long max_chain;   // most sub-steps of one group in one step
   unsigned long long removals;    // bodies removed by rmin / rmax
+  unsigned long long pair_substeps;   // sub-steps the single-pair path took
 };
 
 struct Dev {

@@ -26,6 +26,7 @@ __global__ void k_setup_disk(Dev D, int d) {
   st->max_chain = 0;
   st->merges_reported = 0;
   st->removals = 0;
+  st->pair_substeps = 0;
 }
 
 void launch_setup_disk(const Dev &D, int d, cudaStream_t s) { k_setup_disk<<<1, 32, 0, s>>>(D, d); }

@@ -328,8 +328,10 @@ __device__ void recurse(const GView &S, const GroupCtx &C, const Dev &D, const L
           int plev = S.lev[q];
           const int k0 = k;
           __syncwarp();
+          const long long sub0 = substeps;
           const int rc = pair_run(D, C, lane, V.h, V.cnt, lc, X, Vv, S.gm[a], S.gm[b], R0 * R0,
                                   S.invR0[q], 1.0000001 * (Rc * Rc), k, plev, substeps, deepest);
+          if (lane == 0) atomicAdd(&D.stat[C.d].pair_substeps, (unsigned long long)(substeps - sub0));
           if (lane < 8 && pc < 3) {
             double *px = pc == 0 ? S.x : (pc == 1 ? S.y : S.z);
             double *pv = pc == 0 ? S.vx : (pc == 1 ? S.vy : S.vz);
@@ -1173,8 +1175,10 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
             double X = pc == 0 ? px : (pc == 1 ? py : (pc == 2 ? pz : 0.0));
             double V = pc == 0 ? ux : (pc == 1 ? uy : (pc == 2 ? uz : 0.0));
             int plev = SH(lev, q);
+            const long long sub0 = substeps;
             const int rc = pair_run(D, C, lane, hs, cs, lc, X, V, SH(gm, a_), SH(gm, b_), SH(R0sq, q),
                                     SH(iR0, q), SH(Rcut, q), k, plev, substeps, deepest);
+            if (lane == 0) atomicAdd(&D.stat[C.d].pair_substeps, (unsigned long long)(substeps - sub0));
             const double ax_ = SH(X, 0), ay_ = SH(X, 1), az_ = SH(X, 2);
             const double avx = SH(V, 0), avy = SH(V, 1), avz = SH(V, 2);
             const double bx_ = SH(X, 4), by_ = SH(X, 5), bz_ = SH(X, 6);

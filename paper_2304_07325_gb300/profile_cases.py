@@ -36,7 +36,7 @@ def main(argv=None):
     st = s.stats()
     status = s.sync()
     print(f"case {a.case} status {status} substeps {st.substeps} depth {st.max_depth} "
-          f"longest chain {st.max_chain}")
+          f"longest chain {st.max_chain} single-pair path {st.pair_substeps}")
     for name, ms in zip(PHASES, ph):
         print(f"  {name:28s} {ms:10.3f} ms")
     if st.substeps:

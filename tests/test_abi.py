@@ -41,7 +41,7 @@ def test_param_struct_layout_matches_header(built_lib):
     assert abs(p.G - 39.47841760435743) < 1e-14 and p.m0 == 1.0 and p.precision == 0
     assert p.rmin == 0.0 and p.rmax == 0.0
     assert ctypes.sizeof(sy.symba_params) == 5 * 8 + 6 * 4 + 2 * 8
-    assert ctypes.sizeof(sy.symba_stats) == 4 * 4 + 5 * 8
+    assert ctypes.sizeof(sy.symba_stats) == 4 * 4 + 6 * 8
     assert ctypes.sizeof(sy.symba_schedule) == 4 * 4
     assert ctypes.sizeof(sy.symba_tune_result) == 4 * 4 + 4 * 8 + 4 * 4
 

@@ -80,6 +80,7 @@ def test_bound_pair_group(orc, sy):
     st, calls, depth, rel = out[0]
     assert depth >= 10 and st.max_depth == depth
     assert st.substeps == calls > 10000
+    assert st.pair_substeps > 0.9 * st.substeps      # below level 2 the pair is alone
     E_ref, _ = ref.energy()
     E_gpu, _ = gpu.energy()
     assert abs(E_gpu - E_ref) <= 1e-12 * abs(E_ref)

@@ -58,7 +58,10 @@ def test_variant_steps_from_oracle_states(orc, sy, var):
         spread = np.linalg.norm(twin.x - ref.x, axis=1) / norm
         bad = np.where(rel > np.maximum(1e-12, 100.0 * spread))[0]
         assert len(bad) == 0, [(int(i), rel[i], spread[i]) for i in bad[:5]]
-        deepest = max(deepest, gpu.stats().max_depth)
+        st = gpu.stats()
+        deepest = max(deepest, st.max_depth)
+        if var["l"] != 3:
+            assert st.pair_substeps == 0                # the packed path is specific to l = 3
     assert deepest >= 2
 
 
