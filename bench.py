@@ -168,6 +168,30 @@ def workload(args):
     return d, P
 
 
+def host_cpu():
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: implementer and part), the
+    logical CPUs and those this process may run on."""
+    model = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        names = [ln.split(":", 1)[1].strip() for ln in info if ln.lower().startswith("model name")]
+        if names:
+            model = names[0]
+        else:
+            impl = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")]
+            part = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")]
+            if impl and part:
+                model = f"implementer {impl[0]} part {part[0]}"
+    except OSError:
+        pass
+    try:
+        affinity = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        affinity = None
+    import platform
+    return {"model": model, "arch": platform.machine(), "nproc": os.cpu_count(), "affinity": affinity}
+
+
 def cpu_baseline(args, d, P, budget_s):
     """The oracle, as it stands, on full steps of the same disk until the time budget is spent."""
     import oracle
@@ -182,7 +206,7 @@ def cpu_baseline(args, d, P, budget_s):
         if el >= budget_s or steps >= max(1, args.steps):
             break
     value = 2.0 * P * steps / el
-    return {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+    return {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{steps} full oracle steps of the N={args.n} disk (seed {args.seed}), "
                       f"{el:.1f} s on 1 host core, serial FP64 C"}, steps, el
 
