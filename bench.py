@@ -417,7 +417,9 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
                         "h2d_bytes_per_step": 2 * 8 * 3 * ntot, "d2h_bytes_per_step": 2 * 8 * 3 * ntot,
                         "steps": ne},
-                "gpu_launches": args.steps * 12,
+                # per timed step: the step's 12 kernels plus the per-call statistics reset (the
+                # loop times each step as its own call; the launch list shows the same 13)
+                "gpu_launches": args.steps * 13,
                 "clocks": clk, "wall_s": wall, "second": second}
         print(json.dumps(line), flush=True)
     sysm.close()
