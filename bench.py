@@ -181,7 +181,9 @@ def host_cpu():
             impl = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")]
             part = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")]
             if impl and part:
-                model = f"implementer {impl[0]} part {part[0]}"
+                known = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1",
+                         ("0x41", "0xd0c"): "Arm Neoverse N1", ("0x41", "0xd49"): "Arm Neoverse N2"}
+                model = known.get((impl[0], part[0]), f"implementer {impl[0]} part {part[0]}")
     except OSError:
         pass
     try:
