@@ -110,6 +110,16 @@ int symba_step(symba_ctx *c, int nsteps);
  * bodies merged since the last synchronising call and no error happened). */
 int symba_sync(symba_ctx *c);
 
+/* Advances n independent contexts by nsteps steps each and waits for all of them.  The systems
+ * are not stepped in lock-step: each context keeps exactly one step in flight on its own stream,
+ * and its next step is launched as soon as the last one has completed, so the systems' chains of
+ * recursion sub-steps overlap on the device and none waits for a slower one (a pool, by
+ * contrast, steps every system by the same launches).  Every context must be distinct.  The
+ * calling thread polls completion (short sleeps) until the last step is done.  Returns the worst
+ * status over the contexts as symba_sync does, SYMBA_E_INVAL for a NULL array or context or
+ * negative counts, or the first launch error (contexts may then still have a step in flight). */
+int symba_step_many(symba_ctx *const *ctxs, int n, int nsteps);
+
 /* Total energy E and angular momentum L[3] of the current state (democratic heliocentric, equal
  * to the barycentric totals; Sec. 3 accuracy test).  Each is the correctly rounded sum of its
  * terms.  Synchronises.  E and L are host pointers. */

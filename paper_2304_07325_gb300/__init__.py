@@ -37,7 +37,7 @@ EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "s
             "symba_pool_step", "symba_pool_sync", "symba_pool_get_state", "symba_pool_energy",
             "symba_pool_get_stats", "symba_pool_evict", "symba_pool_free", "symba_status_string",
             "symba_profile_step", "symba_energy_static", "symba_pool_get_schedule",
-            "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune"]
+            "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune", "symba_step_many"]
 SYMBA_NPHASES = 10
 PHASES = ["sun drift + prologue", "kick 1 + encounter check", "kick-1 reduction", "grouping",
           "Kepler drift", "group recursion", "kick 2", "kick-2 reduction", "total momentum",
@@ -122,6 +122,7 @@ def lib():
             "symba_pool_set_schedule": (c_int, [vp, POINTER(symba_schedule)]),
             "symba_pool_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
             "symba_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
+            "symba_step_many": (c_int, [POINTER(c_void_p), c_int, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -349,6 +350,13 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+def step_many(systems, nsteps: int = 1) -> int:
+    """Advances independent systems by nsteps each, every one on its own stream with one step in
+    flight, so that none waits for a slower one (symba_step_many); waits for all."""
+    arr = (c_void_p * len(systems))(*[s._h for s in systems])
+    return _check(lib().symba_step_many(arr, len(systems), int(nsteps)), "symba_step_many")
 
 
 def G_default() -> float:

@@ -2,11 +2,13 @@
 // memory arenas sized at creation, first-fit allocation of particle and pair ranges, the
 // trapezoid tile list, and the per-step launch sequence captured once into a CUDA graph.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -918,6 +920,62 @@ int symba_step(symba_ctx *c, int nsteps) {
 int symba_sync(symba_ctx *c) {
   if (!c) return SYMBA_E_INVAL;
   return slot_status(c->pool, c->slot);
+}
+
+int symba_step_many(symba_ctx *const *ctxs, int n, int nsteps) {
+  if (!ctxs || n < 0 || nsteps < 0) return SYMBA_E_INVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return SYMBA_E_INVAL;
+  if (n == 0 || nsteps == 0) return SYMBA_OK;
+  // one step in flight per context: each context's next step is launched as soon as its last
+  // one has completed, so every stream stays one step deep and no system waits behind another
+  std::vector<cudaEvent_t> ev((size_t)n, nullptr);
+  std::vector<int> left((size_t)n, nsteps);
+  std::vector<char> busy((size_t)n, 0);
+  int rc = SYMBA_OK;
+  for (int i = 0; i < n && rc == SYMBA_OK; ++i) {
+    if (cudaSetDevice(ctxs[i]->pool->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess)
+      rc = SYMBA_E_CUDA;
+  }
+  bool pending = true;
+  while (rc == SYMBA_OK && pending) {
+    bool progressed = false;
+    pending = false;
+    for (int i = 0; i < n && rc == SYMBA_OK; ++i) {
+      if (busy[i]) {
+        const cudaError_t q = cudaEventQuery(ev[i]);
+        if (q == cudaSuccess) {
+          busy[i] = 0;
+          progressed = true;
+        } else if (q != cudaErrorNotReady) {
+          rc = SYMBA_E_CUDA;
+          break;
+        }
+      }
+      if (!busy[i] && left[i] > 0) {
+        symba_pool *P = ctxs[i]->pool;
+        const int r = pool_step(P, 1);
+        if (r != SYMBA_OK) { rc = r; break; }
+        if (cudaEventRecord(ev[i], P->stream) != cudaSuccess) { rc = SYMBA_E_CUDA; break; }
+        busy[i] = 1;
+        --left[i];
+        progressed = true;
+      }
+      pending = pending || busy[i] || left[i] > 0;
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  for (int i = 0; i < n; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (rc != SYMBA_OK) return rc;
+  int worst = SYMBA_OK;
+  for (int i = 0; i < n; ++i) {
+    const int s = slot_status(ctxs[i]->pool, ctxs[i]->slot);
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (s > 0 && worst == SYMBA_OK) worst = s;
+  }
+  return worst;
 }
 
 int symba_energy(symba_ctx *c, double *E, double L[3]) {

@@ -91,3 +91,8 @@ def test_invalid_arguments_are_rejected_before_any_device_call(built_lib):
     assert lib.symba_pool_set_schedule(None, C.byref(sched)) == sy.SYMBA_E_INVAL
     assert lib.symba_pool_autotune(None, 1, C.byref(res)) == sy.SYMBA_E_INVAL
     assert lib.symba_autotune(None, 1, C.byref(res)) == sy.SYMBA_E_INVAL
+    nulls = (C.c_void_p * 2)(None, None)
+    assert lib.symba_step_many(None, 1, 1) == sy.SYMBA_E_INVAL
+    assert lib.symba_step_many(nulls, 2, 1) == sy.SYMBA_E_INVAL
+    assert lib.symba_step_many(nulls, 0, 1) == sy.SYMBA_OK
+    assert lib.symba_step_many(nulls, -1, 1) == sy.SYMBA_E_INVAL

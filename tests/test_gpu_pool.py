@@ -83,3 +83,16 @@ def test_pool_rejects_what_does_not_fit(sy):
     s3 = pool.admit(small.x, small.v, small.m, small.radius)
     assert s3 == s1 and s2 != s1
     pool.close()
+
+
+def test_step_many_equals_each_system_alone(sy):
+    """Independent contexts advanced together by symba_step_many (each on its own stream, one step
+    in flight) end bit for bit where each ends alone."""
+    disks = [disk.planetesimal_disk(n, 5100 + k) for k, n in enumerate([1200, 400, 2500])]
+    systems = [sy.System(d.x, d.v, d.m, d.radius) for d in disks]
+    assert sy.step_many(systems, 5) >= 0
+    for d, s in zip(disks, systems):
+        (xa, va, ma, ra, aa), Ea = _alone(sy, d, 5)
+        x, v, m, r, a = s.get_state()
+        assert np.array_equal(x, xa) and np.array_equal(v, va) and np.array_equal(a, aa)
+        s.close()
