@@ -7,6 +7,10 @@ memory (bodies, trapezoid tiles, pair lists, within an HBM budget) are free; eve
 advances all admitted simulations by one step with the same kernel launches; a simulation that
 has used its step budget is read back and evicted, which frees room for the next arrivals.
 Results do not depend on the mix: every kernel works per system with a fixed summation order.
+
+A ConcurrentServer serves the same requests without lock-step: each admitted simulation sits in
+a resident single-system pool of its own, on its own stream, and advances as soon as its previous
+step has completed, so no simulation waits for another's longest chain of recursion sub-steps.
 """
 from __future__ import annotations
 
@@ -166,6 +170,104 @@ class Server:
 
     def close(self):
         self.pool.close()
+
+
+class ConcurrentServer:
+    """Requests served without lock-step.  `slots` single-system pools stay resident on the
+    device, each with its own stream and each sized for the largest request, so admitting and
+    evicting allocate nothing.  An arrived request takes a free slot; the loop keeps exactly one
+    step in flight per admitted request and launches its next step as soon as that step's
+    completion event has fired, so a request never waits for another's chain of recursion
+    sub-steps (in a Server every pool step waits for the slowest resident).  Each result is that
+    of the request alone: its slot is a pool of one.  Step latencies are taken on the host from a
+    step's launch to the loop turn that sees it complete."""
+
+    def __init__(self, slots: int, max_n: int, precision: int = SYMBA_PRECISION_FP64,
+                 pools=None, streams=None, events=None, clock=time.perf_counter, idle_s: float = 5e-5):
+        if pools is None:
+            import torch
+            streams = [torch.cuda.Stream() for _ in range(slots)]
+            events = [torch.cuda.Event() for _ in range(slots)]
+            pools = [Pool(1, max_n + 64, tiles_for(max_n, max_n), precision, stream=st) for st in streams]
+        self.pools, self.streams, self.events = pools, streams, events
+        self.precision = precision
+        self.clock = clock
+        self.idle_s = idle_s
+        self.free = list(range(len(pools)))[::-1]
+        self.active = {}            # slot -> [request, steps done, admitted_s, in flight, launched_s, pool slot]
+
+    def admit(self, req: Request, now: float) -> bool:
+        if not self.free:
+            return False
+        k = self.free[-1]
+        try:
+            ps = self.pools[k].admit(req.x, req.v, req.m, req.radius, n_massive=req.n_massive, params=req.params)
+        except SymbaError:
+            return False
+        self.free.pop()
+        self.active[k] = [req, 0, now, False, 0.0, ps]
+        return True
+
+    def _retire(self, k: int, now: float, keep_state: bool) -> Result:
+        req, done, t_adm, _, _, ps = self.active.pop(k)
+        pool = self.pools[k]
+        res = Result(rid=req.rid, n=len(req.m), steps=done, admitted_s=t_adm, finished_s=now)
+        if keep_state:
+            res.x, res.v, _, _, res.alive = pool.get_state(ps)
+            res.energy = pool.energy(ps)
+        res.status = pool.stats(ps).status
+        pool.evict(ps)
+        self.free.append(k)
+        return res
+
+    def run(self, requests, keep_state: bool = True, time_scale: float = 1.0, max_wall_s: float | None = None):
+        """Serve `requests` (arrival_s on the wall clock, scaled by time_scale).  Returns the
+        results in completion order and the loop statistics (step_ms: one entry per request
+        step)."""
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        results, stats = [], ServeStats()
+        t0 = self.clock()
+        qi = 0
+        while qi < len(pending) or self.active:
+            now = self.clock() - t0
+            if max_wall_s is not None and now > max_wall_s:
+                break
+            while qi < len(pending) and pending[qi].arrival_s * time_scale <= now:
+                if not self.admit(pending[qi], now):
+                    break
+                qi += 1
+            stats.max_resident = max(stats.max_resident, len(self.active))
+            progressed = False
+            for k in list(self.active):
+                st = self.active[k]
+                if st[3]:
+                    if not self.events[k].query():
+                        continue
+                    t = self.clock() - t0
+                    stats.step_ms.append(1e3 * (t - st[4]))
+                    stats.sim_steps += 1
+                    st[1] += 1
+                    st[3] = False
+                    progressed = True
+                    if st[1] >= st[0].steps:
+                        results.append(self._retire(k, t, keep_state))
+                        continue
+                self.pools[k].step(1)
+                self.events[k].record(self.streams[k])
+                st[3] = True
+                st[4] = self.clock() - t0
+                progressed = True
+            if not progressed:
+                if not self.active and qi < len(pending):
+                    time.sleep(min(0.001, max(0.0, pending[qi].arrival_s * time_scale - now)))
+                else:
+                    time.sleep(self.idle_s)
+        stats.wall_s = self.clock() - t0
+        return results, stats
+
+    def close(self):
+        for p in self.pools:
+            p.close()
 
 
 def poisson_requests(count: int, rate_per_s: float = 20.0, seed: int = 3000, n_lo: int = 500,

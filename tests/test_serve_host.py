@@ -97,3 +97,95 @@ def test_first_come_first_served_and_late_arrivals_wait():
     admits = [ev[1] for ev in pool.log if ev[0] == "admit"]
     assert admits == [0, 0, 0]                  # one slot, reused in arrival order
     assert results[2].admitted_s >= 0.5
+
+
+# --------------------------------------------------------------------------------------------
+# the concurrent server: one step in flight per request, no lock-step
+# --------------------------------------------------------------------------------------------
+class FakeOnePool:
+    """A single-system pool; logs its steps with the shared log."""
+
+    def __init__(self, k, log):
+        self.k, self.log, self.n = k, log, None
+
+    def admit(self, x, v, m, radius, n_massive=None, params=None):
+        assert self.n is None
+        self.n = len(m)
+        self.log.append(("admit", self.k))
+        return 0
+
+    def step(self, n):
+        assert n == 1 and self.n is not None
+        self.log.append(("step", self.k))
+
+    def get_state(self, slot):
+        return np.zeros((self.n, 3)), np.zeros((self.n, 3)), np.zeros(self.n), np.zeros(self.n), np.ones(self.n, dtype=np.int32)
+
+    def energy(self, slot):
+        return -1.0, np.zeros(3)
+
+    def stats(self, slot):
+        return FakeStats()
+
+    def evict(self, slot):
+        self.n = None
+        self.log.append(("evict", self.k))
+
+    def close(self):
+        pass
+
+
+class FakeEvent:
+    """Completes `lag` queries after it was recorded; checks that a step is never launched on a
+    slot whose previous step is still in flight."""
+
+    def __init__(self, lag):
+        self.lag, self.left, self.recorded = lag, 0, False
+
+    def record(self, stream):
+        assert not self.recorded or self.left == 0, "a second step launched while one is in flight"
+        self.recorded, self.left = True, self.lag
+
+    def query(self):
+        if self.left > 0:
+            self.left -= 1
+            return False
+        return True
+
+
+def _conc(lags):
+    from paper_2304_07325_gb300.serve import ConcurrentServer
+    log = []
+    pools = [FakeOnePool(k, log) for k in range(len(lags))]
+    events = [FakeEvent(l) for l in lags]
+    srv = ConcurrentServer(len(lags), 64, pools=pools, streams=[None] * len(lags), events=events,
+                           clock=FakeClock(), idle_s=0.0)
+    return srv, log
+
+
+def test_concurrent_server_runs_every_budget_with_one_step_in_flight():
+    srv, log = _conc([0, 2, 5])
+    reqs = [_req(0, 0.0, 32, 3), _req(1, 0.0, 32, 1), _req(2, 0.0, 32, 4), _req(3, 0.0, 32, 2),
+            _req(4, 0.01, 32, 2)]
+    results, stats = srv.run(reqs)
+    assert {r.rid: r.steps for r in results} == {0: 3, 1: 1, 2: 4, 3: 2, 4: 2}
+    assert stats.sim_steps == 12 and len(stats.step_ms) == 12 and stats.max_resident == 3
+    # every slot is admitted, stepped and evicted in turn, never holding two requests
+    for k in range(3):
+        seq = [e[0] for e in log if e[1] == k]
+        held = 0
+        for e in seq:
+            held += {"admit": 1, "evict": -1}.get(e, 0)
+            assert 0 <= held <= 1
+        assert held == 0
+    assert sorted(srv.free) == [0, 1, 2] and not srv.active
+
+
+def test_concurrent_server_a_slow_request_does_not_hold_back_a_fast_one():
+    srv, log = _conc([40, 0])                   # slot 0's steps take 40 polls, slot 1's none
+    reqs = [_req(0, 0.0, 32, 2), _req(1, 0.0, 32, 5)]
+    results, stats = srv.run(reqs)
+    assert [r.rid for r in results] == [1, 0]   # the fast request finishes first
+    steps = [e[1] for e in log if e[0] == "step"]
+    first_slow_done = steps.index(0, 1)         # the slow slot's second launch
+    assert steps[:first_slow_done].count(1) == 5  # all five fast steps ran meanwhile
