@@ -552,7 +552,7 @@ def run_serve(args):
     srv.close()
     summ = stats.summary()
     # the same stream served without lock-step: one resident single-system pool per slot
-    csrv = ConcurrentServer(32, max_n, precision=prec)
+    csrv = ConcurrentServer(32, max_n, precision=prec, hbm_budget_bytes=64 << 30)
     cres, cstats = csrv.run(reqs, keep_state=False)
     csrv.close()
     csumm = cstats.summary()

@@ -183,8 +183,13 @@ class ConcurrentServer:
     step's launch to the loop turn that sees it complete."""
 
     def __init__(self, slots: int, max_n: int, precision: int = SYMBA_PRECISION_FP64,
-                 pools=None, streams=None, events=None, clock=time.perf_counter, idle_s: float = 5e-5):
+                 hbm_budget_bytes: int | None = None, pools=None, streams=None, events=None,
+                 clock=time.perf_counter, idle_s: float = 5e-5):
         if pools is None:
+            if hbm_budget_bytes is not None:
+                # as many resident slots as the device-memory budget holds at the largest request
+                per_slot = Pool.footprint(max_n, max_n, default_params(precision=precision))
+                slots = max(1, min(slots, hbm_budget_bytes // max(1, per_slot)))
             import torch
             streams = [torch.cuda.Stream() for _ in range(slots)]
             events = [torch.cuda.Event() for _ in range(slots)]

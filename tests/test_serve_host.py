@@ -189,3 +189,28 @@ def test_concurrent_server_a_slow_request_does_not_hold_back_a_fast_one():
     steps = [e[1] for e in log if e[0] == "step"]
     first_slow_done = steps.index(0, 1)         # the slow slot's second launch
     assert steps[:first_slow_done].count(1) == 5  # all five fast steps ran meanwhile
+
+
+def test_concurrent_server_slots_follow_the_memory_budget(monkeypatch):
+    """With a device-memory budget the server keeps as many resident slots as the budget holds
+    at the largest request's footprint (no device needed: the pools are replaced)."""
+    import paper_2304_07325_gb300.serve as serve
+    made = []
+
+    class P:
+        def __init__(self, *a, **k):
+            made.append(a)
+
+        @staticmethod
+        def footprint(n, nm, params=None):
+            return 1000
+
+    class FakeTorch:
+        class cuda:
+            Stream = object
+            Event = object
+
+    monkeypatch.setattr(serve, "Pool", P)
+    monkeypatch.setitem(__import__("sys").modules, "torch", FakeTorch)
+    srv = serve.ConcurrentServer(32, 5000, hbm_budget_bytes=4500)
+    assert len(srv.pools) == 4 and len(made) == 4
