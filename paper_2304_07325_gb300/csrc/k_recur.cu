@@ -875,24 +875,29 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   bool start = true;
   set_level(j);
   sep();
+  deepest = max(deepest, j);
   for (;;) {
     bool level_done = false;
     if (start) {
       {
-        const bool touch = lt_nn(r2, pRcut);
-        if (touch || substeps >= cmax_sub) {     // both rare: one branch
-          if (touch) {
-            rc = 1;
-          } else {
-            ++substeps;
-            rc = 2;
+        // the rare cases of a sub-step's opening under one branch: contact possible, budget
+        // spent, or the forces held are another level's
+        const bool touch = lt_nn(r2, pRcut), over = substeps >= cmax_sub;
+        if (touch || over || fat != j) {
+          if (touch || over) {
+            if (touch) {
+              rc = 1;
+            } else {
+              ++substeps;
+              rc = 2;
+            }
+            break;
           }
-          break;
+          forces_skip();
+          fat = j;
         }
       }
       ++substeps;
-      deepest = max(deepest, j);
-      if (fat != j) { forces_skip(); fat = j; }
       const double U = V;                  // velocities the check sees
       V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
       bool fl = lt_nn(r2, R2);             // inside R_j: the pair is in F_j
@@ -955,6 +960,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         if (j + 1 <= cmax_depth) {
           cs[j] = cj;
           ++j;
+          deepest = max(deepest, j);          // a level is entered only here (and at the start)
           hs[j] = c_pow2 ? hs[j - 1] * c_invM : hs[j - 1] / (double)cM;
           cj = 0;
           set_level(j);
