@@ -208,9 +208,32 @@ def cpu_baseline(args, d, P, budget_s):
         if el >= budget_s or steps >= max(1, args.steps):
             break
     value = 2.0 * P * steps / el
-    return {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": f"{steps} full oracle steps of the N={args.n} disk (seed {args.seed}), "
-                      f"{el:.1f} s on 1 host core, serial FP64 C"}, steps, el
+    cb = {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
+          "sample": f"{steps} full oracle steps of the N={args.n} disk (seed {args.seed}), "
+                    f"{el:.1f} s on 1 host core, serial FP64 C"}
+    cb["parallel_kick"] = parallel_kick(sim, P)
+    return cb, steps, el
+
+
+def parallel_kick(sim, P, budget_s=3.0):
+    """The multi-core CPU reference point for the pair kick: the trapezoid accelerations of the
+    oracle's current state and level-0 list, rows spread over every host thread (OpenMP)."""
+    import oracle
+    pairs, _, _ = sim.enc_groups()
+    args = (sim.x, sim.m, sim.rhill, sim.alive, pairs, sim.n_massive, sim.params)
+    oracle.trap_accel_omp(*args)                   # warm-up (threads, pages)
+    t0 = time.perf_counter()
+    reps, used = 0, 0
+    while True:
+        _, used = oracle.trap_accel_omp(*args)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    t = el / reps
+    return {"pairs_per_s": P / t, "ms_per_kick": 1e3 * t, "threads": used,
+            "kind": "OpenMP trapezoid kick (the oracle's pair arithmetic, rows over threads)",
+            "sample": f"{reps} kicks of {P} pairs in {el:.1f} s"}
 
 
 def run_reference(args):

@@ -4,6 +4,10 @@ The oracle (symba_oracle.c) is a plain, serial FP64 CPU restatement of the SyMBA
 SyMBAp structure of arXiv:2304.07325 (Sec. 2 trapezoid loop and encounter grouping; Sec. 3
 parameters M, R_k/R_{k+1}, l).  Only tests/, the package smoke check and the benchmark's CPU
 baseline may import this package; the library path never does.
+
+trap_omp.c is the benchmark's multi-core CPU reference point for the kick (the same trapezoid
+accelerations with the rows spread over OpenMP threads); it is not the oracle and no parity claim
+rests on it.
 """
 from __future__ import annotations
 
@@ -18,6 +22,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "symba_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "trap_omp.c")
+_OMP_LIB = os.path.join(_HERE, "liboracle_omp.so")
 
 OK, E_INVAL, E_NOMEM, E_KEPLER, E_DEPTH, E_NONFINITE = 0, -1, -2, -4, -5, -7
 MAX_LEVELS = 64
@@ -31,6 +37,47 @@ def build(force: bool = False) -> str:
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile the multi-core trapezoid kick (OpenMP; a serial build if the compiler has none)."""
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC):
+        tmp = _OMP_LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O3", "-std=gnu11", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _OMP_SRC, "-lm"]
+        try:
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
+        os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
+
+
+_omp_lib = None
+
+
+def trap_accel_omp(x, m, rhill, alive, pairs, n_massive: int, params: "Params", threads: int = 0):
+    """Accelerations of the level-0 trapezoid (flagged pairs weighted by g_0, all others 1) on
+    `threads` host threads (0: all OpenMP offers).  Returns (a [n, 3], threads used)."""
+    global _omp_lib
+    if _omp_lib is None:
+        L = ctypes.CDLL(build_omp())
+        dp, ip = POINTER(c_double), POINTER(c_int)
+        L.trap_omp_accel.restype = c_int
+        L.trap_omp_accel.argtypes = [c_int, c_int, dp, dp, dp, ip, ip, c_int, c_double, c_double, c_double,
+                                     c_int, c_int, dp]
+        _omp_lib = L
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    n = xs.shape[0]
+    ms = np.ascontiguousarray(m, dtype=np.float64)
+    rh = np.ascontiguousarray(rhill, dtype=np.float64)
+    al = np.ascontiguousarray(alive, dtype=np.int32)
+    pl = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    a = np.zeros((n, 3))
+    t = _omp_lib.trap_omp_accel(n, int(n_massive), _dp(xs), _dp(ms), _dp(rh), _ip(al), _ip(pl), int(pl.shape[0]),
+                                params.G, params.hill_scale, params.shell_ratio, params.l, int(threads), _dp(a))
+    if t < 1:
+        raise MemoryError("trap_omp_accel: scratch allocation failed")
+    return a, t
 
 
 class Params(ctypes.Structure):
