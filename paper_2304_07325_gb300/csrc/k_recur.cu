@@ -12,8 +12,8 @@
 // body.  The active pairs F_{k-1} and their bodies are kept as nested prefixes of two
 // permutations (stable partition after every check), so deep levels touch only their own pairs.
 //
-// The sub-step chain is latency-bound (GB300 issues one FP64 warp instruction per ~64 cycles per
-// quadrant), so it is kept short:
+// The sub-step chain is latency-bound (GB300 issues one FP64 instruction per ~64 cycles per warp),
+// so it is kept short:
 //   - the group's bodies and pairs are gathered into a member-slot view that lives in shared
 //     memory for groups of up to 32 bodies and 64 pairs (global scratch otherwise), so phases
 //     exchange data through shared memory, and are scattered back at the end;
