@@ -31,8 +31,9 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (no tensor cores for this path)
 FLOPS_PER_PAIR_KICK = 26          # 3 sub, 5 r^2, 2 for 1/sqrt, 2 for r^-3, 2 mass scalings, 12 FMA flops
 FLOPS_PER_PAIR_CHECK = 18
 # The group recursion is a chain of dependent sub-steps per group; the longest chain sets the step
-# time.  Its roofline is the FP64 latency of one warp: a GB300 warp completes one FP64 instruction
-# per DFMA_LATENCY_CYCLES (dependent or not; measured with a dependent DFMA chain), and a chain
+# time.  Its roofline is the FP64 issue rate of one warp: a GB300 warp completes one FP64
+# instruction per DFMA_LATENCY_CYCLES, dependent or not (measured with 1 to 8 independent DFMA
+# chains per warp; the limit is per warp, four warps per SM reach it at once), and a chain
 # sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
 # (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
 DFMA_LATENCY_CYCLES = 64.3
@@ -400,7 +401,7 @@ def run_ours(args):
                     "traffic": RECURSION_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
                     "share_of_step": phase_tot[5] / phase_tot.sum(),
                     "peak_source": f"SM clock {sm_hz / 1e6:.0f} MHz / {DFMA_LATENCY_CYCLES} cycles per "
-                                   "dependent FP64 instruction (measured)",
+                                   "FP64 instruction of one warp, dependent or not (measured)",
                     "fp64_instr_per_chain_substep": FP64_INSTR_PER_CHAIN_SUBSTEP,
                     "us_per_chain_substep": chain_us,
                     "note": "latency-bound: one warp runs a group's dependent sub-steps; the longest "
