@@ -40,11 +40,11 @@ DFMA_LATENCY_CYCLES = 64.3
 FP64_INSTR_PER_CHAIN_SUBSTEP = 34.0
 # DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
 # trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
-KICK_TRAFFIC_BYTES_N10000 = ((1.83 + 13.66) + (1.64 + 12.01)) / 2 * 1e6
+KICK_TRAFFIC_BYTES_N10000 = ((1.8944 + 13.7940) + (1.4029 + 11.9360)) / 2 * 1e6
 # FP64 pipe of the kick kernels busy (ncu sm__pipe_fp64_cycles_active over active cycles, kick 1
 # and kick 2 at N = 10,000, FP64): the issue-side fraction of the FP64 peak
-KICK_FP64_PIPE_ACTIVE_N10000 = (0.8836 + 0.8882) / 2
-RECURSION_TRAFFIC_BYTES_N10000 = 1.43e6 + 20.22e3
+KICK_FP64_PIPE_ACTIVE_N10000 = (0.8836 + 0.8883) / 2
+RECURSION_TRAFFIC_BYTES_N10000 = 1.487872e6 + 18.432e3
 
 
 def parse():
