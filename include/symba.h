@@ -17,7 +17,8 @@
  *   - Particle arrays are indexed 0..n-1, massive bodies first (indices < n_massive), field
  *     (massless) particles after.  Vectors are n x 3 row-major doubles: x0 y0 z0 x1 y1 z1 ...
  *   - A pointer argument may be host memory or device memory of the current device; the library
- *     detects which.  The library copies what it needs and never keeps the caller's pointer.
+ *     detects which.  A pointer into another GPU's memory is rejected with SYMBA_E_INVAL.  The
+ *     library copies what it needs and never keeps the caller's pointer.
  *   - The state the library keeps is democratic heliocentric: heliocentric positions and
  *     barycentric velocities.
  *   - Return values: SYMBA_OK (0), a negative SYMBA_E_* code, or SYMBA_COLLISION (positive,
@@ -137,6 +138,14 @@ int symba_enc_groups(symba_ctx *c, int *pairs, int *group_of_pair, int cap, int 
  * Synchronises. */
 int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radius, int *alive);
 
+/* Copies out the n Hill radii the context uses (host or device array of n doubles): those given
+ * to symba_init, or a_i (m_i / 3 m0)^{1/3} computed there from the osculating heliocentric orbit
+ * (vis-viva with mu = G (m0 + m_i); r_i if unbound; 0 for field particles) with a correctly
+ * rounded cube root, then rescaled by (m / m_i)^{1/3} when body i grows by a merger.  They set
+ * the critical radii lambda (rH_i + rH_j) of the encounter check (Sec. 2, the encounter
+ * paragraph; Sec. 3 for the shell ratio).  Synchronises; returns the sticky status. */
+int symba_get_rhill(symba_ctx *c, double *rhill);
+
 /* Replaces positions (heliocentric) and barycentric velocities; masses, radii and Hill radii
  * stay.  Enqueued on the context's stream.  Also clears the sticky status. */
 int symba_set_state(symba_ctx *c, const double *x, const double *v);
@@ -187,6 +196,7 @@ int symba_pool_sync(symba_pool *pool);
 int symba_pool_get_state(symba_pool *pool, int slot, double *x, double *v, double *m,
                          double *radius, int *alive);
 int symba_pool_energy(symba_pool *pool, int slot, double *E, double L[3]);
+int symba_pool_get_rhill(symba_pool *pool, int slot, double *rhill);
 int symba_pool_get_stats(symba_pool *pool, int slot, symba_stats *s);
 
 /* Removes a system; its slot, bodies and scratch become free for later admissions. */
@@ -260,15 +270,17 @@ const char *symba_status_string(int status);
 /* n_massive..n-1 are field particles.  Enqueued on cuda_stream (NULL = the legacy default      */
 /* stream); returns without waiting.                                                           */
 /* It calls no allocating routine: its exact-sum scratch is a 3,864-byte file-scope device     */
-/* array that every GPU which loads the library holds until the process exits.  The first call */
-/* on a device looks up that array's device address (once per device); make that first call   */
-/* before any stream capture.  All calls share the array and it keeps the last call's contents */
-/* (each call clears it first), so calls that overlap on the GPU -- on different streams, or   */
-/* from different host threads -- race and must be serialised by the caller.                   */
-/* Sizes: the scratch sums at most 2^31 - 1 terms, so n > SYMBA_ENERGY_STATIC_MAX_N is rejected */
-/* with SYMBA_E_INVAL, as are host pointers and n < 1.                                         */
+/* array that every GPU which loads the library holds until the process exits.  Each call asks */
+/* the runtime for that array's device address on the current device (no allocation); the     */
+/* first call on a device may load the library's device code, so make it before any stream    */
+/* capture.  All calls share the array and it keeps the last call's contents (each call       */
+/* clears it first), so calls that overlap on the GPU -- on different streams, or from         */
+/* different host threads -- race and must be serialised by the caller.                        */
+/* Sizes: one accumulator sums at most 2^31 - 1 terms and the energy of n bodies takes         */
+/* n (n - 1)/2 + 2n + 1, so n > SYMBA_ENERGY_STATIC_MAX_N is rejected with SYMBA_E_INVAL, as   */
+/* are n < 1, host pointers and pointers into another GPU's memory.                            */
 /* ---------------------------------------------------------------------------------------- */
-#define SYMBA_ENERGY_STATIC_MAX_N 65535
+#define SYMBA_ENERGY_STATIC_MAX_N 65534
 int symba_energy_static(int n, int n_massive, const double *x, const double *v, const double *m,
                         double G, double m0, double *out, void *cuda_stream);
 

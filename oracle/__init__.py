@@ -127,6 +127,8 @@ def lib():
         L.orc_energy.argtypes = [POINTER(Params), POINTER(_Sim), dp, dp]
         L.orc_velocity_helio.restype = None
         L.orc_velocity_helio.argtypes = [POINTER(Params), POINTER(_Sim), dp]
+        L.orc_cbrt_rn.restype = c_double
+        L.orc_cbrt_rn.argtypes = [c_double]
         L.orc_accel_trapezoid.restype = None
         L.orc_accel_trapezoid.argtypes = [POINTER(Params), POINTER(_Sim), ip, c_int, dp]
         _lib = L
@@ -150,6 +152,11 @@ def make_params(dt=0.5, M=4, shell_ratio=2.08, hill_scale=6.5, l=3, G=4.0 * math
 def fsum(a) -> float:
     a = np.ascontiguousarray(a, dtype=np.float64)
     return lib().orc_fsum(_dp(a), a.size)
+
+
+def cbrt_rn(x: float) -> float:
+    """The correctly rounded cube root (the double nearest the real cube root of x)."""
+    return lib().orc_cbrt_rn(float(x))
 
 
 def partition(x: float, l: int = 3) -> float:

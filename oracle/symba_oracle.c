@@ -390,6 +390,106 @@ int orc_kepler_drift(double mu, double dt, double *x, double *v) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Correctly rounded cube root: the double nearest the real cube root of x (IEEE 754-2008,     */
+/* Sec. 9.2, lists it as rootn(x, 3)).  Hill radii (a (m / 3 m0)^{1/3}) and merged radii       */
+/* ((R_i^3 + R_j^3)^{1/3}) are cube roots; libm's cbrt is only faithful, and one ulp of a      */
+/* radius can decide a strict encounter or contact comparison at a tie, so the value used is   */
+/* the one the definition fixes.                                                                */
+/* Method: start from libm's candidate y and move it to the neighbouring double while x lies   */
+/* outside y's rounding interval.  The cube is increasing, so y = RN(cbrt x) exactly when      */
+/* b_lo^3 < x < b_hi^3, where b_lo and b_hi are the midpoints between y and its neighbours.    */
+/* Each comparison is done on integers: b = B 2^k with B odd (54 bits), x = X 2^e, so          */
+/* b^3 < x  <=>  B^3 < X 2^(e - 3k).  A midpoint's cube is never a double (B^3 is odd and has  */
+/* more than 53 bits), so no comparison is a tie.                                               */
+/* ------------------------------------------------------------------------------------------ */
+#define MW 8 /* 8 x 32-bit words: 256 bits, more than the 165 a 55-bit cube or 53-bit x 2^t needs */
+
+static void mw_from_u64(uint32_t a[MW], uint64_t v) {
+  memset(a, 0, sizeof(uint32_t) * MW);
+  a[0] = (uint32_t)v;
+  a[1] = (uint32_t)(v >> 32);
+}
+
+/* r = a * b (schoolbook, words least significant first; the product must fit in MW words) */
+static void mw_mul(uint32_t r[MW], const uint32_t a[MW], const uint32_t b[MW]) {
+  uint32_t t[2 * MW];
+  memset(t, 0, sizeof(t));
+  for (int i = 0; i < MW; ++i) {
+    uint64_t carry = 0;
+    for (int j = 0; j < MW; ++j) {
+      uint64_t cur = (uint64_t)a[i] * b[j] + t[i + j] + carry;
+      t[i + j] = (uint32_t)cur;
+      carry = cur >> 32;
+    }
+    t[i + MW] = (uint32_t)carry;
+  }
+  memcpy(r, t, sizeof(uint32_t) * MW);
+}
+
+/* r = v * 2^s */
+static void mw_shl(uint32_t r[MW], uint64_t v, int s) {
+  memset(r, 0, sizeof(uint32_t) * MW);
+  for (int bit = 0; bit < 64; ++bit) {
+    if ((v >> bit) & 1u) {
+      int pos = bit + s;
+      if (pos >= 0 && pos < 32 * MW) r[pos / 32] |= (uint32_t)1u << (pos % 32);
+    }
+  }
+}
+
+static int mw_cmp(const uint32_t a[MW], const uint32_t b[MW]) {
+  for (int i = MW - 1; i >= 0; --i) {
+    if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+  }
+  return 0;
+}
+
+/* sign of (B 2^k)^3 - X 2^e, for 2^53 - 1 <= B < 2^55 and 0 < X < 2^53 */
+static int cube_minus(uint64_t B, int k, uint64_t X, int e) {
+  int t = e - 3 * k;
+  /* B^3 lies in [2^158, 2^165): X 2^t is below it for t < 0 and above it for t > 203 */
+  if (t < 0) return 1;
+  if (t > 32 * MW - 53) return -1;
+  uint32_t b[MW], b2[MW], b3[MW], rhs[MW];
+  mw_from_u64(b, B);
+  mw_mul(b2, b, b);
+  mw_mul(b3, b2, b);
+  mw_shl(rhs, X, t);
+  return mw_cmp(b3, rhs);
+}
+
+/* x = X 2^e with X an integer (x finite, positive) */
+static void split_double(double x, uint64_t *X, int *e) {
+  int ex;
+  double f = frexp(x, &ex);            /* x = f 2^ex, f in [0.5, 1) */
+  *X = (uint64_t)ldexp(f, 53);         /* exact: f has at most 53 significant bits */
+  *e = ex - 53;
+}
+
+double orc_cbrt_rn(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  if (x < 0.0) return -orc_cbrt_rn(-x);
+  uint64_t X;
+  int e;
+  split_double(x, &X, &e);
+  double y = cbrt(x);
+  for (int it = 0; it < 8; ++it) {
+    uint64_t Y;
+    int ey;
+    split_double(y, &Y, &ey);          /* y = Y 2^ey, Y in [2^52, 2^53) (y is always normal) */
+    /* upper boundary (y + next up) / 2 = (2Y + 1) 2^(ey - 1) */
+    if (cube_minus(2 * Y + 1, ey - 1, X, e) < 0) { y = nextafter(y, INFINITY); continue; }
+    /* lower boundary (next down + y) / 2: (2Y - 1) 2^(ey - 1), or (2^54 - 1) 2^(ey - 2) when y
+       is a power of two (the spacing below it is half the spacing above) */
+    uint64_t Bl = Y == (1ull << 52) ? (1ull << 54) - 1 : 2 * Y - 1;
+    int kl = Y == (1ull << 52) ? ey - 2 : ey - 1;
+    if (cube_minus(Bl, kl, X, e) > 0) { y = nextafter(y, 0.0); continue; }
+    break;
+  }
+  return y;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Democratic-heliocentric bookkeeping.                                                        */
 /* ------------------------------------------------------------------------------------------ */
 
@@ -420,7 +520,8 @@ static void sun_drift(const orc_params *P, orc_sim *s, double h) {
 
 /* Init: barycentric velocities v_i = v_i^hel - S / (m0 + Mt), with S = sum m_j v_j^hel and    */
 /* Mt = sum m_j (both correctly rounded); Hill radii rH_i = a_i (m_i / (3 m0))^{1/3} with a_i  */
-/* the osculating heliocentric semi-major axis for mu = G (m0 + m_i) (or r_i if unbound).      */
+/* the osculating heliocentric semi-major axis for mu = G (m0 + m_i) (or r_i if unbound), from */
+/* vis-viva 1/a = 2/r - v^2/mu; the cube root is the correctly rounded one (orc_cbrt_rn).       */
 void orc_init(const orc_params *P, orc_sim *s, const double *v_helio, int compute_rhill) {
   orc_acc a;
   acc_init(&a);
@@ -444,7 +545,7 @@ void orc_init(const orc_params *P, orc_sim *s, const double *v_helio, int comput
       double mu = P->G * (P->m0 + s->m[i]);
       double inv_a = 2.0 / r - v2 / mu;
       double a_i = inv_a > 0.0 ? 1.0 / inv_a : r;
-      s->rhill[i] = a_i * cbrt(s->m[i] / (3.0 * P->m0));
+      s->rhill[i] = a_i * orc_cbrt_rn(s->m[i] / (3.0 * P->m0));
     }
   }
   s->status = ORC_OK;
@@ -592,8 +693,8 @@ static void merge_pair(orc_sim *s, int i, int j) {
     }
   }
   double Ri = s->radius[i], Rj = s->radius[j];
-  s->radius[i] = cbrt(Ri * Ri * Ri + Rj * Rj * Rj);
-  if (mi > 0.0) s->rhill[i] = s->rhill[i] * cbrt(M / mi);
+  s->radius[i] = orc_cbrt_rn(Ri * Ri * Ri + Rj * Rj * Rj);
+  if (mi > 0.0) s->rhill[i] = s->rhill[i] * orc_cbrt_rn(M / mi);
   s->m[i] = M;
   s->m[j] = 0.0;
   s->radius[j] = 0.0;

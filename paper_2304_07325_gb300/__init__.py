@@ -29,7 +29,7 @@ SYMBA_E_NONFINITE = -7
 SYMBA_COLLISION = 1
 SYMBA_PRECISION_FP64 = 0
 SYMBA_PRECISION_MIXED = 1
-SYMBA_ENERGY_STATIC_MAX_N = 65535
+SYMBA_ENERGY_STATIC_MAX_N = 65534
 
 EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "symba_energy",
             "symba_enc_groups", "symba_get_state", "symba_set_state", "symba_get_stats",
@@ -37,7 +37,8 @@ EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "s
             "symba_pool_step", "symba_pool_sync", "symba_pool_get_state", "symba_pool_energy",
             "symba_pool_get_stats", "symba_pool_evict", "symba_pool_free", "symba_status_string",
             "symba_profile_step", "symba_energy_static", "symba_pool_get_schedule",
-            "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune", "symba_step_many"]
+            "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune", "symba_step_many",
+            "symba_get_rhill", "symba_pool_get_rhill"]
 SYMBA_NPHASES = 10
 PHASES = ["sun drift + prologue", "kick 1 + encounter check", "kick-1 reduction", "grouping",
           "Kepler drift", "group recursion", "kick 2", "kick-2 reduction", "total momentum",
@@ -123,6 +124,8 @@ def lib():
             "symba_pool_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
             "symba_autotune": (c_int, [vp, c_int, POINTER(symba_tune_result)]),
             "symba_step_many": (c_int, [POINTER(c_void_p), c_int, c_int]),
+            "symba_get_rhill": (c_int, [vp, vp]),
+            "symba_pool_get_rhill": (c_int, [vp, c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -227,6 +230,12 @@ class System:
         _check(lib().symba_get_state(self._h, _ptr(x), _ptr(v), _ptr(m), _ptr(r), _ptr(a)), "symba_get_state")
         return x, v, m, r, a
 
+    def rhill(self) -> np.ndarray:
+        """The Hill radii the context uses (symba_get_rhill)."""
+        rh = np.zeros(self.n)
+        _check(lib().symba_get_rhill(self._h, _ptr(rh)), "symba_get_rhill")
+        return rh
+
     def set_state(self, x, v_bary):
         xs, vs = _host(x, np.float64, (-1, 3)), _host(v_bary, np.float64, (-1, 3))
         _check(lib().symba_set_state(self._h, _ptr(xs), _ptr(vs)), "symba_set_state")
@@ -314,6 +323,11 @@ class Pool:
         s = symba_stats()
         _check(lib().symba_pool_get_stats(self._h, int(slot), byref(s)), "symba_pool_get_stats")
         return s
+
+    def rhill(self, slot: int) -> np.ndarray:
+        rh = np.zeros(self.n[slot])
+        _check(lib().symba_pool_get_rhill(self._h, int(slot), _ptr(rh)), "symba_pool_get_rhill")
+        return rh
 
     def autotune(self, reps: int = 3) -> dict:
         """Times the launch schedules on the admitted systems and keeps the fastest

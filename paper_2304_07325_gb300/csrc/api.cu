@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "ptr_class.h"
 
 namespace {
 
@@ -112,15 +113,11 @@ int dalloc(symba_pool *P, T **ptr, size_t count) {
   return SYMBA_OK;
 }
 
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// a device array of the current device (or managed memory): used in place
+bool is_device_ptr(const void *p) { return pointer_class(p) == PTR_DEVICE; }
+
+// an array in another GPU's memory: rejected by every entry point
+bool is_foreign_ptr(const void *p) { return p && pointer_class(p) == PTR_FOREIGN; }
 
 // device copy of a caller array (or the array itself when it is already on the device)
 struct Staged {
@@ -131,7 +128,9 @@ struct Staged {
 
 int stage_in(Staged &s, const void *src, size_t bytes, cudaStream_t st) {
   if (!src) return SYMBA_OK;
-  if (is_device_ptr(src)) { s.dev = src; return SYMBA_OK; }
+  const int cls = pointer_class(src);
+  if (cls == PTR_FOREIGN) return SYMBA_E_INVAL;
+  if (cls == PTR_DEVICE) { s.dev = src; return SYMBA_OK; }
   if (cudaMalloc(&s.own, bytes ? bytes : 1) != cudaSuccess) return SYMBA_E_NOMEM;
   CK(cudaMemcpyAsync(s.own, src, bytes, cudaMemcpyHostToDevice, st));
   s.dev = s.own;
@@ -466,6 +465,8 @@ int get_state(symba_pool *P, int d, double *x, double *v, double *m, double *rad
   if (!valid_slot(P, d)) return SYMBA_E_INVAL;
   CK(cudaSetDevice(P->device));
   const int n = P->slots[d].n;
+  if (is_foreign_ptr(x) || is_foreign_ptr(v) || is_foreign_ptr(m) || is_foreign_ptr(rad) || is_foreign_ptr(alive))
+    return SYMBA_E_INVAL;
   double *dx = nullptr, *dv = nullptr, *dm = nullptr, *dr = nullptr;
   int *da = nullptr;
   const bool hx = x && !is_device_ptr(x), hv = v && !is_device_ptr(v), hm = m && !is_device_ptr(m),
@@ -480,7 +481,8 @@ int get_state(symba_pool *P, int d, double *x, double *v, double *m, double *rad
   tmp(hr, (void **)&dr, sizeof(double) * n);
   tmp(ha, (void **)&da, sizeof(int) * n);
   if (st == SYMBA_OK) {
-    launch_gather_state(P->D, d, n, hx ? dx : x, hv ? dv : v, hm ? dm : m, hr ? dr : rad, ha ? da : alive, P->stream);
+    launch_gather_state(P->D, d, n, hx ? dx : x, hv ? dv : v, hm ? dm : m, hr ? dr : rad, ha ? da : alive,
+                        nullptr, P->stream);
     if (hx) cudaMemcpyAsync(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, P->stream);
     if (hv) cudaMemcpyAsync(v, dv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, P->stream);
     if (hm) cudaMemcpyAsync(m, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream);
@@ -490,6 +492,22 @@ int get_state(symba_pool *P, int d, double *x, double *v, double *m, double *rad
   }
   cudaFree(dx); cudaFree(dv); cudaFree(dm); cudaFree(dr); cudaFree(da);
   if (st != SYMBA_OK) return st;
+  return slot_status(P, d);
+}
+
+int get_rhill(symba_pool *P, int d, double *rh) {
+  if (!valid_slot(P, d) || !rh) return SYMBA_E_INVAL;
+  CK(cudaSetDevice(P->device));
+  const int n = P->slots[d].n;
+  if (is_foreign_ptr(rh)) return SYMBA_E_INVAL;
+  const bool host = !is_device_ptr(rh);
+  double *dh = nullptr;
+  if (host && cudaMalloc(&dh, sizeof(double) * n) != cudaSuccess) return SYMBA_E_NOMEM;
+  launch_gather_state(P->D, d, n, nullptr, nullptr, nullptr, nullptr, nullptr, host ? dh : rh, P->stream);
+  if (host) cudaMemcpyAsync(rh, dh, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream);
+  const cudaError_t e = cudaStreamSynchronize(P->stream);
+  cudaFree(dh);
+  if (e != cudaSuccess) return SYMBA_E_CUDA;
   return slot_status(P, d);
 }
 
@@ -540,6 +558,7 @@ __global__ void k_pairs_out(Dev D, int d, int cap, int *pairs, int *gop) {
 int enc_groups(symba_pool *P, int d, int *pairs, int *gop, int cap, int *npairs, int *ngroups) {
   if (!valid_slot(P, d) || cap < 0) return SYMBA_E_INVAL;
   CK(cudaSetDevice(P->device));
+  if (is_foreign_ptr(pairs) || is_foreign_ptr(gop)) return SYMBA_E_INVAL;
   DiskStat st;
   int r = read_stat(P, d, &st);
   if (r != SYMBA_OK) return r;
@@ -992,6 +1011,13 @@ int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radiu
   if (!c) return SYMBA_E_INVAL;
   return get_state(c->pool, c->slot, x, v, m, radius, alive);
 }
+
+int symba_get_rhill(symba_ctx *c, double *rhill) {
+  if (!c) return SYMBA_E_INVAL;
+  return get_rhill(c->pool, c->slot, rhill);
+}
+
+int symba_pool_get_rhill(symba_pool *pool, int slot, double *rhill) { return get_rhill(pool, slot, rhill); }
 
 int symba_set_state(symba_ctx *c, const double *x, const double *v) {
   if (!c) return SYMBA_E_INVAL;

@@ -149,6 +149,79 @@ __device__ __forceinline__ double rsqrt_fp64(double r2) {
   return rsqrt(r2);
 }
 
+// Correctly rounded cube root: the double nearest the real cube root (IEEE 754-2008 Sec. 9.2,
+// rootn(x, 3)).  Hill radii a (m / 3 m0)^{1/3} and merged radii (R_a^3 + R_b^3)^{1/3} are cube
+// roots, and a radius feeds strict encounter and contact comparisons, so it takes the one value
+// the definition fixes rather than the library's faithful (1-ulp) result.  The library value is
+// the starting candidate y; since t -> t^3 is increasing, y is the nearest double exactly when
+// x lies strictly between the cubes of y's rounding boundaries (the midpoints to its
+// neighbours), and y moves one double up or down until it does.  A boundary is B 2^k with B an
+// odd integer below 2^55 and x = X 2^e with X below 2^53, so b^3 < x  <=>  B^3 < X 2^(e - 3k),
+// compared on 192-bit integers (three 64-bit words).  B^3 is odd with more than 53 significant
+// bits, so it never equals X 2^(e - 3k): no ties.  Off the hot path (set-up and mergers).
+struct U192 {
+  unsigned long long w0, w1, w2;   // least significant first
+};
+
+__device__ __forceinline__ U192 cube_u192(unsigned long long B) {
+  const unsigned long long s0 = B * B, s1 = __umul64hi(B, B);          // B^2 < 2^110
+  const unsigned long long a0 = s0 * B, a1 = __umul64hi(s0, B);
+  const unsigned long long b0 = s1 * B, b1 = __umul64hi(s1, B);
+  U192 r;
+  r.w0 = a0;
+  r.w1 = a1 + b0;
+  r.w2 = b1 + (r.w1 < a1 ? 1ull : 0ull);
+  return r;
+}
+
+// sign of B^3 - X 2^t for 2^53 - 1 <= B < 2^55 (B^3 in [2^158, 2^165)) and 0 < X < 2^53
+__device__ __forceinline__ int cube_cmp(unsigned long long B, unsigned long long X, int t) {
+  if (t < 0) return 1;
+  if (t > 192 - 53) return -1;
+  U192 rhs = {0ull, 0ull, 0ull};
+  const int q = t >> 6, s = t & 63;
+  const unsigned long long lo = X << s, hi = s ? (X >> (64 - s)) : 0ull;
+  if (q == 0) { rhs.w0 = lo; rhs.w1 = hi; }
+  else if (q == 1) { rhs.w1 = lo; rhs.w2 = hi; }
+  else { rhs.w2 = lo; }
+  const U192 c = cube_u192(B);
+  if (c.w2 != rhs.w2) return c.w2 < rhs.w2 ? -1 : 1;
+  if (c.w1 != rhs.w1) return c.w1 < rhs.w1 ? -1 : 1;
+  if (c.w0 != rhs.w0) return c.w0 < rhs.w0 ? -1 : 1;
+  return 0;
+}
+
+static __device__ __noinline__ double cbrt_rn(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  const bool negative = x < 0.0;
+  const double ax = fabs(x);
+  const unsigned long long xb = (unsigned long long)__double_as_longlong(ax);
+  const int xe = (int)(xb >> 52);
+  const unsigned long long X = xe ? ((xb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : xb;
+  const int e = (xe ? xe : 1) - 1075;                     // ax = X 2^e (subnormals included)
+  double y = cbrt(ax);                                    // within one ulp; always normal
+  for (int it = 0; it < 8; ++it) {
+    const unsigned long long yb = (unsigned long long)__double_as_longlong(y);
+    const unsigned long long Y = (yb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int ey = (int)(yb >> 52) - 1075;                // y = Y 2^ey
+    // upper boundary (2Y + 1) 2^(ey - 1): below the root -> y is too small
+    if (cube_cmp(2 * Y + 1, X, e - 3 * (ey - 1)) < 0) {
+      y = __longlong_as_double((long long)(yb + 1));
+      continue;
+    }
+    // lower boundary: (2Y - 1) 2^(ey - 1), or (2^54 - 1) 2^(ey - 2) below a power of two
+    const bool pow2 = Y == (1ull << 52);
+    const unsigned long long Bl = pow2 ? (1ull << 54) - 1 : 2 * Y - 1;
+    const int kl = pow2 ? ey - 2 : ey - 1;
+    if (cube_cmp(Bl, X, e - 3 * kl) > 0) {
+      y = __longlong_as_double((long long)(yb - 1));
+      continue;
+    }
+    break;
+  }
+  return negative ? -y : y;
+}
+
 // Order of non-negative doubles through their bit patterns (an integer comparison instead of an
 // FP64-pipe one; valid for +0, finite and +inf operands).
 __device__ __forceinline__ bool lt_nn(double a, double b) {
@@ -569,7 +642,7 @@ void launch_energy(const Dev &D, int d, const LaunchCfg &L, unsigned long long *
                    cudaStream_t s);
 void launch_energy_round(unsigned long long *acc, double *out4, cudaStream_t s);
 void launch_gather_state(const Dev &D, int d, int n, double *x, double *v, double *m, double *rad,
-                         int *alive, cudaStream_t s);
+                         int *alive, double *rh, cudaStream_t s);
 void launch_scatter_state(const Dev &D, int d, int n, const double *x, const double *v,
                           cudaStream_t s);
 void launch_prologue(const Dev &D, int ndisks, cudaStream_t s);

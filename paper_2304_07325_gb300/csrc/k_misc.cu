@@ -64,7 +64,8 @@ void launch_discard(const Dev &D, long long npart, cudaStream_t s) {
 // --------------------------------------------------------------------------------------------
 // initial upload: heliocentric -> barycentric velocities with exact sums
 //   v_i = v_i^hel - S / (m0 + Mt),  S = sum m_j v_j^hel,  Mt = sum m_j   (each correctly rounded)
-// and Hill radii rH_i = a_i (m_i / 3 m0)^{1/3} from the osculating heliocentric orbit.
+// and Hill radii rH_i = a_i (m_i / 3 m0)^{1/3} from the osculating heliocentric orbit
+// (vis-viva 1/a = 2/r - v^2/mu, mu = G (m0 + m_i); r if unbound; correctly rounded cube root).
 // --------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_init_sums(Dev D, int d, int n, const double *vh,
                                                    const double *m, double *q_out) {
@@ -110,7 +111,7 @@ __global__ void k_init_state(Dev D, int d, int n, const double *xh, const double
         const double mu = __dmul_rn(dd.G, __dadd_rn(dd.m0, mi));
         const double inv_a = __dsub_rn(__ddiv_rn(2.0, r), __ddiv_rn(v2, mu));
         const double a = inv_a > 0.0 ? __ddiv_rn(1.0, inv_a) : r;
-        h = __dmul_rn(a, cbrt(__ddiv_rn(mi, __dmul_rn(3.0, dd.m0))));
+        h = __dmul_rn(a, cbrt_rn(__ddiv_rn(mi, __dmul_rn(3.0, dd.m0))));
       } else {
         h = rh[i];
       }
@@ -389,7 +390,8 @@ void launch_drift(const Dev &D, long long npart, cudaStream_t s) {
 // --------------------------------------------------------------------------------------------
 // state transfer (n x 3 row-major <-> SoA)
 // --------------------------------------------------------------------------------------------
-__global__ void k_gather(Dev D, int d, int n, double *x, double *v, double *m, double *rad, int *alive) {
+__global__ void k_gather(Dev D, int d, int n, double *x, double *v, double *m, double *rad, int *alive,
+                         double *rh) {
   const int off = D.disks[d].off;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int p = off + i;
@@ -398,6 +400,7 @@ __global__ void k_gather(Dev D, int d, int n, double *x, double *v, double *m, d
     if (m) m[i] = D.m[p];
     if (rad) rad[i] = D.rad[p];
     if (alive) alive[i] = D.alive[p];
+    if (rh) rh[i] = D.rh[p];
   }
 }
 
@@ -411,8 +414,8 @@ __global__ void k_scatter(Dev D, int d, int n, const double *x, const double *v)
 }
 
 void launch_gather_state(const Dev &D, int d, int n, double *x, double *v, double *m, double *rad,
-                         int *alive, cudaStream_t s) {
-  k_gather<<<64, 256, 0, s>>>(D, d, n, x, v, m, rad, alive);
+                         int *alive, double *rh, cudaStream_t s) {
+  k_gather<<<64, 256, 0, s>>>(D, d, n, x, v, m, rad, alive, rh);
 }
 
 void launch_scatter_state(const Dev &D, int d, int n, const double *x, const double *v,

@@ -117,8 +117,8 @@ __device__ void merge_pair(const GView &S, const GroupCtx &C, const Dev &D, int 
     S.vz[a] = __ddiv_rn(__dadd_rn(__dmul_rn(ma, S.vz[a]), __dmul_rn(mb, S.vz[b])), M);
   }
   const double Ra = S.rad[a], Rb = S.rad[b];
-  S.rad[a] = cbrt(__dadd_rn(__dmul_rn(__dmul_rn(Ra, Ra), Ra), __dmul_rn(__dmul_rn(Rb, Rb), Rb)));
-  if (ma > 0.0) S.rh[a] = __dmul_rn(S.rh[a], cbrt(__ddiv_rn(M, ma)));
+  S.rad[a] = cbrt_rn(__dadd_rn(__dmul_rn(__dmul_rn(Ra, Ra), Ra), __dmul_rn(__dmul_rn(Rb, Rb), Rb)));
+  if (ma > 0.0) S.rh[a] = __dmul_rn(S.rh[a], cbrt_rn(__ddiv_rn(M, ma)));
   S.m[a] = M;
   S.gm[a] = __dmul_rn(C.G, M);
   S.m[b] = 0.0;
@@ -1138,8 +1138,8 @@ __device__ void run_group_regs(const Dev &D, const GroupCtx &C, int lane, double
               vy = __ddiv_rn(__dadd_rn(__dmul_rn(ma, vya_), __dmul_rn(mb, vyb_)), Mt);
               vz = __ddiv_rn(__dadd_rn(__dmul_rn(ma, vza_), __dmul_rn(mb, vzb_)), Mt);
             }
-            rad = cbrt(__dadd_rn(__dmul_rn(__dmul_rn(ra_, ra_), ra_), __dmul_rn(__dmul_rn(rb_, rb_), rb_)));
-            if (ma > 0.0) rh = __dmul_rn(rha, cbrt(__ddiv_rn(Mt, ma)));
+            rad = cbrt_rn(__dadd_rn(__dmul_rn(__dmul_rn(ra_, ra_), ra_), __dmul_rn(__dmul_rn(rb_, rb_), rb_)));
+            if (ma > 0.0) rh = __dmul_rn(rha, cbrt_rn(__ddiv_rn(Mt, ma)));
             m = Mt;
             gm = __dmul_rn(C.G, Mt);
           }

@@ -8,12 +8,19 @@
 // array below, which every GPU that loads the library holds until the process exits.
 //
 // The accumulator slots are 64-bit carry-save digits that each absorb at most 2^31 - 1
-// additions of 32-bit chunks, so a call may sum at most 2^31 - 1 terms: n (n - 1)/2 + 2n + 1 of
-// them for n bodies, hence the limit SYMBA_ENERGY_STATIC_MAX_N = 65,535.
+// additions of 32-bit chunks, so a call may sum at most 2^31 - 1 terms into one accumulator: the
+// energy takes n (n - 1)/2 + 2n + 1 of them for n bodies, hence the limit
+// SYMBA_ENERGY_STATIC_MAX_N = 65,534 (checked below at compile time).
 #include <algorithm>
-#include <mutex>
 
 #include "internal.cuh"
+#include "ptr_class.h"
+
+constexpr long long energy_terms(long long n) { return n * (n - 1) / 2 + 2 * n + 1; }
+static_assert(energy_terms(SYMBA_ENERGY_STATIC_MAX_N) <= 2147483647LL,
+              "the energy accumulator of the largest accepted n must take at most 2^31 - 1 terms");
+static_assert(energy_terms(SYMBA_ENERGY_STATIC_MAX_N + 1) > 2147483647LL,
+              "SYMBA_ENERGY_STATIC_MAX_N is the largest n the accumulator allows");
 
 // 7 accumulators (E, Lx, Ly, Lz, Px, Py, Pz) of SA_NDIG + 1 slots: 3,864 bytes
 #define STATIC_ACCS 7
@@ -21,33 +28,21 @@ static __device__ __align__(256) unsigned long long g_static_energy_scratch[STAT
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-unsigned long long *g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
-
-// device address of the scratch array on the current device (set up once per device)
+// Device address of the scratch array on the current device.  In host code the array's name is
+// a host-side stand-in, not a device address, so the address is asked of the runtime (with that
+// device current) at every call: the lookup allocates nothing, and a module reloaded after a
+// device reset gets its new address instead of a stale cached one.  The first lookup on a device
+// may load the module, which is why the first call there should precede any stream capture.
 int scratch_address(unsigned long long **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SYMBA_E_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return SYMBA_E_INVAL;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_static_energy_scratch) != cudaSuccess) return SYMBA_E_CUDA;
-    g_scratch_addr[dev] = (unsigned long long *)ptr;
-  }
-  *out = g_scratch_addr[dev];
+  void *ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_static_energy_scratch) != cudaSuccess) return SYMBA_E_CUDA;
+  *out = (unsigned long long *)ptr;
   return SYMBA_OK;
 }
 
-bool on_device(const void *p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// a device array of the current device (or managed memory); host arrays and other GPUs' arrays
+// are refused
+bool on_device(const void *p) { return pointer_class(p) == PTR_DEVICE; }
 
 }  // namespace
 

@@ -18,15 +18,15 @@ def sy():
     return m
 
 
-def _mixed(sy, d, rhill):
+def _mixed(sy, d):
     p = sy.default_params(precision=sy.SYMBA_PRECISION_MIXED)
-    return sy.System(d.x, d.v, d.m, d.radius, n_massive=d.n_massive, params=p, rhill=rhill)
+    return sy.System(d.x, d.v, d.m, d.radius, n_massive=d.n_massive, params=p)
 
 
 def test_mixed_one_step_encounters_exact_positions_close(orc, sy):
     d = disk.planetesimal_disk(1000, 1000)
     ref = orc.OracleSim(d.x, d.v, d.m, d.radius)
-    gpu = _mixed(sy, d, ref.rhill)
+    gpu = _mixed(sy, d)
     assert ref.step(1) >= 0
     gpu.step(1)
     assert gpu.sync() >= 0
@@ -44,7 +44,7 @@ def test_mixed_field_particles_against_fp64(orc, sy):
     agree to the stated bounds."""
     d = disk.planetesimal_disk(300, 1003, n_field=3000)
     ref = orc.OracleSim(d.x, d.v, d.m, d.radius, n_massive=300)
-    gpu = _mixed(sy, d, ref.rhill)
+    gpu = _mixed(sy, d)
     E0, _ = ref.energy()
     assert ref.step(1) >= 0
     gpu.step(1)

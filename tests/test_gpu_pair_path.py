@@ -43,7 +43,8 @@ def _close(x, ref, twin, tol=1e-12, factor=100.0):
 
 def _run(orc, sy, x, v, m, radius, steps):
     ref = orc.OracleSim(x, v, m, radius)
-    gpu = sy.System(x, v, m, radius, rhill=ref.rhill)
+    gpu = sy.System(x, v, m, radius)
+    assert np.array_equal(gpu.rhill(), ref.rhill)
     out = []
     for _ in range(steps):
         twin = _twin(orc, x, v, m, radius, ref.rhill, ref)
@@ -104,7 +105,8 @@ def test_pair_on_collision_course_merges(orc, sy):
     v = np.array([vc + [0.02, 0.0, 0.0], vc - [0.02, 0.0, 0.0]])
     radius = np.array([1e-5, 1e-5])
     ref = orc.OracleSim(x, v, m, radius)
-    gpu = sy.System(x, v, m, radius, rhill=ref.rhill)
+    gpu = sy.System(x, v, m, radius)
+    assert np.array_equal(gpu.rhill(), ref.rhill)
     assert ref.step(1) >= 0
     gpu.step(1)
     assert gpu.sync() >= 0
@@ -122,7 +124,7 @@ def test_depth_limit_inside_the_pair_path(orc, sy):
     oracle, drifts the pair at the deepest allowed level: same sub-steps, same positions."""
     x, v, m, radius = _binary()
     ref = orc.OracleSim(x, v, m, radius, params=orc.make_params(max_depth=4))
-    gpu = sy.System(x, v, m, radius, rhill=ref.rhill, params=sy.default_params(max_depth=4))
+    gpu = sy.System(x, v, m, radius, params=sy.default_params(max_depth=4))
     twin = orc.OracleSim(x, v, m, radius, rhill=ref.rhill, params=orc.make_params(max_depth=4, noise=1))
     assert ref.step(1) == orc.E_DEPTH
     twin.step(1)

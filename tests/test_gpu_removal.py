@@ -47,7 +47,8 @@ def _system():
 def test_removal_matches_the_oracle(orc, sy):
     x, v, m, rad, nm = _system()
     ref = orc.OracleSim(x, v, m, rad, n_massive=nm, params=orc.make_params(**LIMITS))
-    gpu = sy.System(x, v, m, rad, n_massive=nm, rhill=ref.rhill, params=sy.default_params(**LIMITS))
+    gpu = sy.System(x, v, m, rad, n_massive=nm, params=sy.default_params(**LIMITS))
+    assert np.array_equal(gpu.rhill(), ref.rhill)
     removed = 0
     for step in range(3):
         twin = orc.OracleSim(x, v, m, rad, n_massive=nm, rhill=ref.rhill,

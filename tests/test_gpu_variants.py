@@ -34,7 +34,7 @@ def sy():
 def test_variant_steps_from_oracle_states(orc, sy, var):
     d = disk.planetesimal_disk(1000, 1000)
     ref = orc.OracleSim(d.x, d.v, d.m, d.radius, params=orc.make_params(**var))
-    gpu = sy.System(d.x, d.v, d.m, d.radius, rhill=ref.rhill, params=sy.default_params(**var))
+    gpu = sy.System(d.x, d.v, d.m, d.radius, params=sy.default_params(**var))
     deepest = 0
     for _ in range(8):
         twin = orc.OracleSim(d.x, d.v, d.m, d.radius, rhill=ref.rhill,

@@ -638,3 +638,72 @@ def test_head_on_collision_merges_conserving_mass_and_momentum(orc):
     assert np.linalg.norm(sim.x[0] - com.x[0]) < 1e-8
     E, L = sim.energy()
     assert np.isfinite(E) and np.all(np.isfinite(L))
+
+
+# --------------------------------------------------------------------------------------------
+# correctly rounded cube root (Hill radii and merged radii), pinned by exact rational arithmetic
+# --------------------------------------------------------------------------------------------
+def _is_nearest_cbrt(x: float, y: float) -> bool:
+    """y is the double nearest the real cube root of x > 0: x lies strictly between the cubes of
+    the midpoints from y to its neighbours (exact rationals; the cube is increasing)."""
+    from fractions import Fraction
+    X, Y = Fraction(x), Fraction(y)
+    hi = (Y + Fraction(math.nextafter(y, math.inf))) / 2
+    lo = (Y + Fraction(math.nextafter(y, 0.0))) / 2
+    return lo ** 3 < X < hi ** 3
+
+
+def test_cbrt_rn_is_the_nearest_double(orc):
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    xs = [float(t) * 2.0 ** int(e) for t, e in zip(rng.uniform(0.5, 1.0, 3000), rng.integers(-1074, 1024, 3000))]
+    xs = [x for x in xs if 0.0 < x < math.inf]
+    xs += [5e-324, 2.2250738585072014e-308, 2.225073858507201e-308, 1.7976931348623157e308]
+    # the hardest inputs: x = RN(b^3) for midpoints b between neighbouring doubles, whose cube roots
+    # sit within a hair of a rounding boundary
+    for y in rng.uniform(1.0, 2.0, 3000) * 2.0 ** rng.integers(-300, 300, 3000):
+        b = (Fraction(float(y)) + Fraction(math.nextafter(float(y), math.inf))) / 2
+        xs.append(float(b ** 3))
+    # the disk's mass ratios m / 3 m0 and merged-radius sums
+    d = disk.planetesimal_disk(2000, 77)
+    xs += [float(t) for t in d.m / 3.0] + [float(t) for t in d.radius[:-1] ** 3 + d.radius[1:] ** 3]
+    for x in xs:
+        y = orc.cbrt_rn(x)
+        assert _is_nearest_cbrt(x, y), x
+        assert orc.cbrt_rn(-x) == -y
+    # exact cubes have exact roots; zero and non-finite values pass through
+    for k in range(-40, 41):
+        assert orc.cbrt_rn(float(k) ** 3) == float(k)
+        assert orc.cbrt_rn(8.0 ** k) == 2.0 ** k
+    assert orc.cbrt_rn(0.0) == 0.0 and math.copysign(1.0, orc.cbrt_rn(-0.0)) == -1.0
+    assert orc.cbrt_rn(math.inf) == math.inf and math.isnan(orc.cbrt_rn(math.nan))
+
+
+def test_hill_radius_from_the_osculating_orbit(orc):
+    """rH_i = a_i (m_i / 3 m0)^{1/3}, a_i the heliocentric semi-major axis of the two-body orbit
+    with mu = G (m0 + m_i): bodies placed on orbits of known a (circular and eccentric, from
+    orbital elements with that mu) give it to rounding; an unbound body uses its distance; a field
+    particle has none.  A heavy body and m0 != 1 make each ingredient visible: mu = G m0 moves a
+    by ~m/m0, m/m0 instead of m/3m0 moves rH by 3^{1/3}."""
+    rng = np.random.default_rng(3)
+    for m0 in (1.0, 2.5):
+        P = orc.make_params(m0=m0)
+        xs, vs, ms, want = [], [], [], []
+        for m in (1e-3 * m0, 3e-8 * m0, 0.02 * m0):
+            mu = G * (m0 + m)
+            for a, e in ((5.0, 0.0), (12.5, 0.0), (7.0, 0.3), (19.0, 0.8)):
+                inc, node, peri, M = rng.uniform(0, 1.0), *rng.uniform(0, 2 * math.pi, 3)
+                x, v = disk.elements_to_state(a, e, inc, node, peri, M, mu)
+                xs.append(x); vs.append(v); ms.append(m)
+                want.append(a * (m / (3.0 * m0)) ** (1.0 / 3.0))
+            # unbound: 1.5x the escape speed at r = 8
+            r = 8.0
+            xs.append([0.0, r, 0.0]); vs.append([1.5 * math.sqrt(2.0 * mu / r), 0.0, 0.0]); ms.append(m)
+            want.append(r * (m / (3.0 * m0)) ** (1.0 / 3.0))
+        xs.append([9.0, 0.0, 0.0]); vs.append([0.0, math.sqrt(G * m0 / 9.0), 0.0]); ms.append(0.0)
+        want.append(0.0)
+        n = len(ms)
+        sim = orc.OracleSim(np.array(xs), np.array(vs), np.array(ms), np.zeros(n), n_massive=n, params=P)
+        rel = np.abs(sim.rhill - np.array(want)) / np.maximum(np.array(want), 1e-300)
+        assert rel.max() < 2e-15, rel
+        assert sim.rhill[-1] == 0.0
