@@ -27,24 +27,24 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (no tensor cores for this path)
 FLOPS_PER_PAIR_KICK = 26          # 3 sub, 5 r^2, 2 for 1/sqrt, 2 for r^-3, 2 mass scalings, 12 FMA flops
 FLOPS_PER_PAIR_CHECK = 18
-# The group recursion is a chain of dependent sub-steps per group; the longest chain sets the step
-# time.  Its roofline is the FP64 issue rate of one warp: a GB300 warp completes one FP64
-# instruction per DFMA_LATENCY_CYCLES, dependent or not (measured with 1 to 8 independent DFMA
-# chains per warp; the limit is per warp, four warps per SM reach it at once), and a chain
-# sub-step of the single-pair path executes FP64_INSTR_PER_CHAIN_SUBSTEP FP64 warp instructions
-# (ncu smsp__inst_executed_pipe_fp64.sum over the sub-steps of the bound-pair group).
-DFMA_LATENCY_CYCLES = 64.3
-FP64_INSTR_PER_CHAIN_SUBSTEP = 34.0
-# DRAM read + write per launch at N = 10,000, FP64 (one-pass ncu captures of one step): the
-# trapezoid kick (mean of kick 1 and kick 2) and the group recursion (first step)
-KICK_TRAFFIC_BYTES_N10000 = ((1.8944 + 13.7940) + (1.4029 + 11.9360)) / 2 * 1e6
-# FP64 pipe of the kick kernels busy (ncu sm__pipe_fp64_cycles_active over active cycles, kick 1
-# and kick 2 at N = 10,000, FP64): the issue-side fraction of the FP64 peak
-KICK_FP64_PIPE_ACTIVE_N10000 = (0.8836 + 0.8883) / 2
-RECURSION_TRAFFIC_BYTES_N10000 = 1.487872e6 + 18.432e3
+# FP64 warp instructions of the group recursion per sub-step, by path: least-squares fit of ncu's
+# smsp__inst_executed_pipe_fp64.sum per k_recursion launch against the launches' per-path sub-step
+# counts over four steps of the N = 10,000 disk (residuals <= 1.1 %; profiles/k_recursion_fp64_fit.md).
+# A general sub-step of a large group covers every body and pair of the group.
+FP64_PER_PAIR_SUBSTEP = 27.65
+FP64_PER_GENERAL_SUBSTEP = 933.0
+# The recursion of the bound-pair group the profiles use (bodies of the N = 10,000 disk, seed 1002)
+BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
+# DRAM read + write per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, N = 10,000, FP64)
+# of the current kernels; None until a capture of the current kernel is on record
+RECURSION_TRAFFIC_BYTES = None
+KICK_TRAFFIC_BYTES = None
+# Step size at which the batched and served forms and the one-at-a-time form all keep the energy
+# error of every merger-free disk below 1e-10 (measured on the 64 batched disks: 5.7e-11 after 20
+# steps at 0.125 yr, 1.1e-10 at 0.2, 5.2e-10 at 0.5)
+MATCHED_TAU = 0.125
 
 
 def parse():
@@ -74,6 +74,13 @@ def parse():
     ap.add_argument("--second-n", type=int, default=5000,
                     help="single mode: also time this disk size (0 = off), reported under 'second'")
     ap.add_argument("--second-seed", type=int, default=1001)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="single mode: skip the 64-disk batched comparison at matched accuracy")
+    ap.add_argument("--no-served", action="store_true",
+                    help="single mode: skip the served Poisson stream at matched accuracy")
+    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--served-requests", type=int, default=24)
+    ap.add_argument("--served-steps-cap", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched mode: keep the default launch schedule instead of autotuning it")
     return ap.parse_args()
@@ -196,11 +203,20 @@ def host_cpu():
     return {"model": model, "arch": platform.machine(), "nproc": os.cpu_count(), "affinity": affinity}
 
 
+def workload_name(args, seed=None):
+    """The workload string both arms print (rank 0's seed; replicas add 1000 per rank)."""
+    return (f"planetesimal disk N_m={args.n} + {args.n_field} field, "
+            f"{'FP64' if args.precision == 'fp64' else 'FP32-pair/FP64-state'}, dt=0.5 yr, M=4, "
+            f"R_k/R_k+1=2.08, l=3 (seed {args.seed if seed is None else seed})")
+
+
 def cpu_baseline(args, d, P, budget_s):
-    """The oracle, as it stands, on full steps of the same disk until the time budget is spent."""
+    """The oracle, as it stands, on full steps of the same disk: the same warm-up steps as the GPU
+    arm untimed, then timed steps until the time budget is spent (the GPU arm's first timed steps)."""
     import oracle
     oracle.build()
     sim = oracle.OracleSim(d.x, d.v, d.m, d.radius, n_massive=d.n_massive)
+    sim.step(args.warmup)
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -211,8 +227,8 @@ def cpu_baseline(args, d, P, budget_s):
             break
     value = 2.0 * P * steps / el
     cb = {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
-          "sample": f"{steps} full oracle steps of the N={args.n} disk (seed {args.seed}), "
-                    f"{el:.1f} s on 1 host core, serial FP64 C"}
+          "sample": f"steps {args.warmup}..{args.warmup + steps - 1} of the N={args.n} disk (seed {args.seed}) "
+                    f"after {args.warmup} untimed steps: {el:.1f} s on 1 host core, serial FP64 C"}
     cb["parallel_kick"] = parallel_kick(sim, P)
     return cb, steps, el
 
@@ -239,19 +255,34 @@ def parallel_kick(sim, P, budget_s=3.0):
 
 
 def run_reference(args):
+    """The oracle on the GPU arm's step window: `warmup` untimed steps, then exactly `steps`
+    timed steps of the same disk (serial FP64 C on one host core)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle
+    oracle.build()
     d, P = workload(args)
-    cb, steps, el = cpu_baseline(args, d, P, budget_s=min(150.0, max(10.0, 2.0 * args.cpu_budget_s)))
-    line = {"impl": "reference", "metric": "pair-interactions/s", "value": cb["value"],
-            "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": steps, "warmup": 0,
-            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+    sim = oracle.OracleSim(d.x, d.v, d.m, d.radius, n_massive=d.n_massive)
+    if sim.step(args.warmup) < 0:
+        raise RuntimeError("oracle warm-up failed")
+    t0 = time.perf_counter()
+    st = sim.step(args.steps)
+    el = time.perf_counter() - t0
+    if st < 0:
+        raise RuntimeError("oracle steps failed")
+    value = 2.0 * P * args.steps / el
+    cb = {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
+          "sample": f"steps {args.warmup}..{args.warmup + args.steps - 1} of the workload after {args.warmup} "
+                    f"untimed steps (the GPU arm's window): {el:.1f} s on 1 host core, serial FP64 C"}
+    cb["parallel_kick"] = parallel_kick(sim, P)
+    line = {"impl": "reference", "metric": "pair-interactions/s", "value": value,
+            "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"planetesimal disk N_m={args.n} + {args.n_field} field, FP64, dt=0.5 yr, "
-                                   f"M=4, R_k/R_k+1=2.08, l=3 (seed {args.seed})"},
+            "config": {"workload": workload_name(args)},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -292,6 +323,154 @@ def time_second_disk(sy, disk, n, seed, steps, warmup, stream, flush):
             "us_per_chain_substep_median": statistics.median(chain) if chain else None}
 
 
+def _energy_errors(E0, E1, merges):
+    """|E1 - E0| / |E0| per system; systems with a merger (inelastic: energy is not conserved)
+    are counted apart from the integration error of the others."""
+    dE = [abs((b - a) / a) for a, b in zip(E0, E1)]
+    clean = [e for e, m in zip(dE, merges) if m == 0]
+    return {"max_no_merger": max(clean) if clean else None,
+            "median_no_merger": statistics.median(clean) if clean else None,
+            "systems_no_merger": len(clean), "max_all": max(dE) if dE else None,
+            "le_1e-10": bool(clean) and max(clean) <= 1e-10}
+
+
+def bench_batched(sy, disk, steps, warmup, serial_steps):
+    """Config-4 shape: 64 disks (N log-uniform 1,000-10,000, seeds 2000+k, all massive) at the
+    matched-accuracy step size, as (a) independent contexts advanced by symba_step_many (FP64 and
+    mixed), (b) one pool stepped by shared launches (mixed), (c) one simulation per launch sequence,
+    FP64, one disk at a time.  Sim-steps/s of each, and each form's energy error per disk."""
+    import torch
+    from paper_2304_07325_gb300.serve import tiles_for
+    sizes = disk.batch_sizes(64, 2000, 1000, 10000)
+    disks = [disk.planetesimal_disk(n, 2000 + k) for k, n in enumerate(sizes)]
+    out = {"workload": f"64 planetesimal disks, N log-uniform 1,000-10,000 (seeds 2000+k), all massive, "
+                       f"dt={MATCHED_TAU} yr, M=4, R_k/R_k+1=2.08, l=3", "sizes": sizes, "dt": MATCHED_TAU,
+           "steps": steps, "warmup": warmup}
+    for name, prec in (("step_many_fp64", sy.SYMBA_PRECISION_FP64), ("step_many_mixed", sy.SYMBA_PRECISION_MIXED)):
+        ctxs = [sy.System(d.x, d.v, d.m, d.radius, params=sy.default_params(dt=MATCHED_TAU, precision=prec))
+                for d in disks]
+        E0 = [c.energy()[0] for c in ctxs]
+        sy.step_many(ctxs, warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sy.step_many(ctxs, steps)
+        t = time.perf_counter() - t0
+        E1 = [c.energy()[0] for c in ctxs]
+        merges = [c.stats().merges for c in ctxs]
+        out[name] = {"value": len(disks) * steps / t, "unit": "sim-steps/s",
+                     "energy_error": _energy_errors(E0, E1, merges)}
+        for c in ctxs:
+            c.close()
+    prec = sy.SYMBA_PRECISION_MIXED
+    pool = sy.Pool(len(disks), sum(d.n for d in disks) + 32 * len(disks), sum(tiles_for(d.n, d.n) for d in disks), prec)
+    slots = [pool.admit(d.x, d.v, d.m, d.radius, params=sy.default_params(dt=MATCHED_TAU, precision=prec))
+             for d in disks]
+    E0 = [pool.energy(k)[0] for k in slots]
+    pool.step(warmup)
+    pool.sync()
+    torch.cuda.synchronize()
+    step_ms = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        pool.step(1)
+        pool.sync()
+        step_ms.append(1e3 * (time.perf_counter() - t0))
+    E1 = [pool.energy(k)[0] for k in slots]
+    merges = [pool.stats(k).merges for k in slots]
+    out["pool_mixed"] = {"value": len(disks) * steps / (sum(step_ms) / 1e3), "unit": "sim-steps/s",
+                         "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+                         "energy_error": _energy_errors(E0, E1, merges)}
+    pool.close()
+    # one simulation per launch sequence, one disk at a time (FP64): its trajectory is the
+    # step_many FP64 one, bit for bit (tests/test_gpu_pool.py), hence the same energy error
+    t_serial = 0.0
+    for d in disks:
+        s1 = sy.System(d.x, d.v, d.m, d.radius, params=sy.default_params(dt=MATCHED_TAU))
+        s1.step(warmup)
+        s1.sync()
+        t0 = time.perf_counter()
+        s1.step(serial_steps)
+        s1.sync()
+        t_serial += time.perf_counter() - t0
+        s1.close()
+    serial = len(disks) * serial_steps / t_serial
+    out["one_at_a_time_fp64"] = {"value": serial, "unit": "sim-steps/s", "steps_each": serial_steps,
+                                 "energy_error": "that of step_many_fp64 (the same trajectories, bit for bit)"}
+    for k in ("step_many_fp64", "step_many_mixed", "pool_mixed"):
+        out[k]["speedup_vs_one_at_a_time_fp64"] = out[k]["value"] / serial
+    return out
+
+
+def bench_served(sy, count, steps_cap, serial_steps):
+    """Config-5 shape: Poisson arrivals (20/s), N log-uniform 500-20,000, step budgets U[100, 5000]
+    capped for a bounded run, mixed-precision kick, served by the concurrent server (resident
+    single-system pools, one stream each, one step in flight per request) at the matched-accuracy
+    step size; against the same requests one at a time in FP64."""
+    from paper_2304_07325_gb300.serve import ConcurrentServer, poisson_requests
+    prec = sy.SYMBA_PRECISION_MIXED
+    reqs = poisson_requests(count, 20.0, 3000, 500, 20000, 100, 5000, steps_cap=steps_cap,
+                            params=sy.default_params(dt=MATCHED_TAU, precision=prec))
+    max_n = max(len(r.m) for r in reqs)
+    srv = ConcurrentServer(32, max_n, precision=prec, hbm_budget_bytes=64 << 30)
+    results, stats = srv.run(reqs, keep_state=True)
+    srv.close()
+    summ = stats.summary()
+    E0, E1, merges = [], [], []
+    for res in results:
+        r = reqs[res.rid]
+        s0 = sy.System(r.x, r.v, r.m, r.radius, n_massive=r.n_massive, params=r.params)
+        E0.append(s0.energy()[0])
+        s0.close()
+        E1.append(res.energy[0])
+        merges.append(res.merges)
+    t_serial, n_serial = 0.0, 0
+    for r in reqs:
+        s1 = sy.System(r.x, r.v, r.m, r.radius, n_massive=r.n_massive, params=sy.default_params(dt=MATCHED_TAU))
+        k = min(serial_steps, r.steps)
+        t0 = time.perf_counter()
+        s1.step(k)
+        s1.sync()
+        t_serial += time.perf_counter() - t0
+        n_serial += k
+        s1.close()
+    serial = n_serial / t_serial
+    return {"workload": f"{count} Poisson requests (20/s), N log-uniform 500-20,000, step budgets U[100,5000] "
+                        f"capped at {steps_cap}, dt={MATCHED_TAU} yr, FP32-pair kick, FP64 state",
+            "server": "concurrent: resident single-system pools, one stream each, one step in flight per request",
+            "value": summ["sim_steps_per_s"], "unit": "sim-steps/s", "completed": len(results),
+            "p50_step_ms": summ["p50_step_ms"], "p99_step_ms": summ["p99_step_ms"],
+            "step_latency": "per request step, launch to observed completion", "wall_s": summ["wall_s"],
+            "max_resident": summ["max_resident"], "energy_error": _energy_errors(E0, E1, merges),
+            "one_at_a_time_fp64": {"value": serial, "unit": "sim-steps/s",
+                                   "sample": f"the first min({serial_steps}, budget) steps of each request alone"},
+            "speedup_vs_one_at_a_time_fp64": summ["sim_steps_per_s"] / serial}
+
+
+def chain_vs_cpu(sy, disk):
+    """The dominant kernel's chain against one host core: one step of the bound-pair group (five
+    bodies of the N = 10,000 disk, one dependent chain of ~34,000 sub-steps), recursion time per
+    sub-step on the GPU and the oracle's whole-step time per sub-step on this host."""
+    import oracle
+    d = disk.planetesimal_disk(10000, 1002)
+    g = BOUND_PAIR_GROUP
+    s = sy.System(d.x[g], d.v[g], d.m[g], d.radius[g])
+    s.profile_step(1)
+    s.close()
+    s = sy.System(d.x[g], d.v[g], d.m[g], d.radius[g])
+    ph = s.profile_step(1)
+    st = s.stats()
+    s.close()
+    ref = oracle.OracleSim(d.x[g], d.v[g], d.m[g], d.radius[g])
+    t0 = time.perf_counter()
+    ref.step(1)
+    t = time.perf_counter() - t0
+    n_orc = sum(ref.level_calls)
+    return {"case": "one step of bodies [1244, 3406, 4643, 5122, 9870] of the N=10,000 disk (seed 1002)",
+            "gpu_substeps": int(st.substeps), "gpu_us_per_substep": 1e3 * ph[5] / max(1, st.substeps),
+            "oracle_substeps": n_orc, "oracle_us_per_substep": 1e6 * t / max(1, n_orc),
+            "oracle_host": host_cpu()["model"]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -307,6 +486,8 @@ def run_ours(args):
     from paper_2304_07325_gb300 import build
     build.build()
     stream = torch.cuda.current_stream(dev)
+    # the device rates the roofline divides by, measured now on this GPU (a few milliseconds)
+    rates = sy.measure_rates()
 
     # every rank integrates its own replica (independent disks: replicas, no exchange)
     seed = args.seed + 1000 * rank
@@ -393,37 +574,44 @@ def run_ours(args):
 
     if rank == 0:
         kick_ms = (phase_tot[1] + phase_tot[6]) / (2 * args.steps)
-        kick_flops = FLOPS_PER_PAIR_KICK * P
-        kick_achieved = kick_flops / (kick_ms * 1e-3) / 1e12
-        rec_ms = phase_tot[5] / args.steps
-        peak_note = "GB300 FP64 1.25 TFLOP/s (recipe's figure; a DFMA loop measured 1.19 here)"
-        # the dominant kernel by time: the group recursion, bound by the FP64 latency of the warp
-        # that runs the longest chain of dependent sub-steps
+        kick_tflops = FLOPS_PER_PAIR_KICK * P / (kick_ms * 1e-3) / 1e12
+        fp64_tflops = rates["fp64_flops"] / 1e12
+        rec_s = phase_tot[5] * 1e-3
         sm_hz = 1e6 * (clk.get("sm_mhz") or 2070.0)
-        chain_peak = sm_hz / DFMA_LATENCY_CYCLES / 1e6                    # M FP64 instr/s, one warp
+        # the dominant kernel: the group recursion.  Its FP64 warp instructions per step are the
+        # run's own per-path sub-step counts times the per-path counts ncu measured
+        gen_substeps = substeps - pair_substeps
+        fp64_instr = FP64_PER_PAIR_SUBSTEP * pair_substeps + FP64_PER_GENERAL_SUBSTEP * gen_substeps
+        chip_peak = rates["fp64_flops"] / 64.0          # FP64 warp instructions/s (32 lanes x 2 flops)
+        rec_achieved = fp64_instr / rec_s if rec_s > 0 else 0.0
         chain_us = statistics.median(chain_us_list) if chain_us_list else float("nan")
-        chain_achieved = FP64_INSTR_PER_CHAIN_SUBSTEP / chain_us         # M FP64 instr/s
+        chain_peak = sm_hz / rates["warp_dfma_dep_cycles"]                # one warp, FP64 instr/s
+        chain_achieved = FP64_PER_PAIR_SUBSTEP / (chain_us * 1e-6)
+        traffic_ok = args.n == 10000 and args.n_field == 0 and prec == 0
         roofline = {"kernel": "k_recursion (per-group recursive sub-stepping)", "bound": "alu",
-                    "achieved": chain_achieved, "peak": chain_peak,
-                    "unit": "M FP64 warp-instr/s on the longest group chain (one warp)",
-                    "frac": chain_achieved / chain_peak,
-                    "traffic": RECURSION_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
+                    "achieved": rec_achieved, "peak": chip_peak, "unit": "FP64 warp-instructions/s",
+                    "frac": rec_achieved / chip_peak, "traffic": RECURSION_TRAFFIC_BYTES if traffic_ok else None,
                     "share_of_step": phase_tot[5] / phase_tot.sum(),
-                    "peak_source": f"SM clock {sm_hz / 1e6:.0f} MHz / {DFMA_LATENCY_CYCLES} cycles per "
-                                   "FP64 instruction of one warp, dependent or not (measured)",
-                    "fp64_instr_per_chain_substep": FP64_INSTR_PER_CHAIN_SUBSTEP,
-                    "us_per_chain_substep": chain_us,
-                    "note": "latency-bound: one warp runs a group's dependent sub-steps; the longest "
-                            "chain sets the step time; the rest of each sub-step is shuffles, branches "
-                            "and issue"}
-        roofline_kick = {"kernel": "k_trap_fp64 (trapezoid pair kick)", "bound": "alu", "achieved": kick_achieved,
-                         "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                         "frac": kick_achieved / FP64_PEAK_TFLOPS_NOMINAL,
-                         "traffic": KICK_TRAFFIC_BYTES_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
-                         "ms_per_launch": kick_ms, "peak_source": peak_note,
-                         "fp64_pipe_active": KICK_FP64_PIPE_ACTIVE_N10000 if args.n == 10000 and args.n_field == 0 and prec == 0 else None,
-                         "fp64_pipe_active_source": "ncu sm__pipe_fp64_cycles_active (kick 1, kick 2), "
-                                                    "profiles/k_trap_fp64_disk_N10000.md"}
+                    "peak_source": f"measured by symba_measure_rates in this run: {fp64_tflops:.4f} TFLOP/s FP64 "
+                                   "(independent FMAs on every SM) / 64 flops per warp instruction",
+                    "fp64_instr_per_step": fp64_instr / args.steps,
+                    "fp64_instr_model": f"{FP64_PER_PAIR_SUBSTEP} per single-pair sub-step x {pair_substeps} + "
+                                        f"{FP64_PER_GENERAL_SUBSTEP} per general sub-step x {gen_substeps} "
+                                        "(this run's counts; per-path figures from ncu, "
+                                        "profiles/k_recursion_fp64_fit.md)",
+                    "chain": {"what": "the longest group's dependent chain on one warp against one warp's FP64 "
+                                      "issue (one instruction per warp_dfma_dep_cycles, measured)",
+                              "achieved": chain_achieved, "peak": chain_peak, "unit": "FP64 instr/s, one warp",
+                              "frac": chain_achieved / chain_peak, "us_per_chain_substep": chain_us,
+                              "warp_dfma_dep_cycles": rates["warp_dfma_dep_cycles"]},
+                    "note": "latency-bound: each group's sub-steps are one dependent chain on one warp, and the "
+                            "longest chain sets the step time, so most of the chip's FP64 lanes idle"}
+        roofline_kick = {"kernel": "k_trap_fp64 (trapezoid pair kick)", "bound": "alu", "achieved": kick_tflops,
+                         "peak": fp64_tflops, "unit": "TFLOP/s", "frac": kick_tflops / fp64_tflops,
+                         "traffic": KICK_TRAFFIC_BYTES if traffic_ok else None,
+                         "algorithmic_bytes": 32 * (args.n + args.n_field) + 48 * (args.n + args.n_field),
+                         "ms_per_launch": kick_ms, "flops_per_pair": FLOPS_PER_PAIR_KICK,
+                         "peak_source": "measured by symba_measure_rates in this run (FP64 FMAs on every SM)"}
         phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
         second = None
         if args.second_n > 0 and world == 1 and args.n_field == 0 and prec == 0:
@@ -432,13 +620,18 @@ def run_ours(args):
         cb = None
         if not args.no_cpu_baseline and world == 1:
             cb, _, _ = cpu_baseline(args, d, P, args.cpu_budget_s)
+        chain = chain_vs_cpu(sy, disk) if world == 1 and not args.no_cpu_baseline else None
+        # spec target 2: batched and served forms against one simulation per launch
+        # sequence, FP64, at a step size where every form keeps the energy error <= 1e-10
+        batched = None if args.no_batched or world > 1 else bench_batched(sy, disk, args.batched_steps, 2, 3)
+        served = None if args.no_served or world > 1 else bench_served(sy, args.served_requests,
+                                                                          args.served_steps_cap, 3)
         line = {"metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-pair/f64-state", "data": "synthetic",
-                "config": {"workload": f"planetesimal disk N_m={args.n} + {args.n_field} field, "
-                                       f"{'FP64' if prec == 0 else 'FP32-pair/FP64-state'}, dt=0.5 yr, M=4, "
-                                       f"R_k/R_k+1=2.08, l=3 (seed {args.seed}+1000*rank)",
+                "config": {"workload": workload_name(args),
+                           "seeds": f"{args.seed} + 1000 * rank (replicas)" if world > 1 else str(args.seed),
                            "n": args.n, "pairs_per_kick": P, "l2": "flushed between steps (256 MB write)"
                            if flush is not None else "not flushed",
                            "parallelism": f"replicas x{world}"},
@@ -456,7 +649,8 @@ def run_ours(args):
                 # per timed step: the step's 12 kernels plus the per-call statistics reset (the
                 # loop times each step as its own call; the launch list shows the same 13)
                 "gpu_launches": args.steps * 13,
-                "clocks": clk, "wall_s": wall, "second": second}
+                "clocks": clk, "wall_s": wall, "second": second, "rates": rates,
+                "chain_vs_cpu": chain, "batched": batched, "served": served}
         print(json.dumps(line), flush=True)
     sysm.close()
     if world > 1:

@@ -197,6 +197,9 @@ int symba_pool_get_state(symba_pool *pool, int slot, double *x, double *v, doubl
                          double *radius, int *alive);
 int symba_pool_energy(symba_pool *pool, int slot, double *E, double L[3]);
 int symba_pool_get_rhill(symba_pool *pool, int slot, double *rhill);
+int symba_pool_enc_groups(symba_pool *pool, int slot, int *pairs, int *group_of_pair, int cap,
+                          int *n_pairs, int *n_groups);
+int symba_pool_set_state(symba_pool *pool, int slot, const double *x, const double *v);
 int symba_pool_get_stats(symba_pool *pool, int slot, symba_stats *s);
 
 /* Removes a system; its slot, bodies and scratch become free for later admissions. */
@@ -258,6 +261,19 @@ int symba_autotune(symba_ctx *c, int reps, symba_tune_result *out);
 
 /* Human-readable name of a status code. */
 const char *symba_status_string(int status);
+
+/* Measures, on the current device, the rates that bound this path (measurement infrastructure:
+ * the paper reports only wall-clock times, Sec. 3; the pair kick of Sec. 2 is FP64-pipe bound
+ * and the per-group recursion is bound by one warp's dependent FP64 work).  Writes out[0..5]
+ * (host): 0 the device's FP64 FLOP/s (independent fused multiply-adds on every SM, an FMA
+ * counting 2 flops); 1 cycles per FMA of one warp's dependent FMA chain; 2 cycles per FMA of one
+ * warp running four independent chains; 3 cycles per round trip of a value between two warps of
+ * a CTA through shared memory and two named barriers; 4 multiprocessors; 5 the device's nominal
+ * SM clock in Hz (0 if the runtime does not report it).  Allocates and frees a few bytes, runs
+ * for a few milliseconds on the legacy default stream and synchronises.  Returns SYMBA_OK,
+ * SYMBA_E_INVAL (NULL out), SYMBA_E_NOMEM or SYMBA_E_CUDA. */
+#define SYMBA_NRATES 6
+int symba_measure_rates(double *out);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Energy without device allocation.  The paper has no counterpart: this entry point exists    */

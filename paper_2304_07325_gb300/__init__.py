@@ -38,7 +38,8 @@ EXPORTED = ["symba_default_params", "symba_init", "symba_step", "symba_sync", "s
             "symba_pool_get_stats", "symba_pool_evict", "symba_pool_free", "symba_status_string",
             "symba_profile_step", "symba_energy_static", "symba_pool_get_schedule",
             "symba_pool_set_schedule", "symba_pool_autotune", "symba_autotune", "symba_step_many",
-            "symba_get_rhill", "symba_pool_get_rhill"]
+            "symba_get_rhill", "symba_pool_get_rhill", "symba_measure_rates", "symba_pool_enc_groups",
+            "symba_pool_set_state"]
 SYMBA_NPHASES = 10
 PHASES = ["sun drift + prologue", "kick 1 + encounter check", "kick-1 reduction", "grouping",
           "Kepler drift", "group recursion", "kick 2", "kick-2 reduction", "total momentum",
@@ -126,6 +127,9 @@ def lib():
             "symba_step_many": (c_int, [POINTER(c_void_p), c_int, c_int]),
             "symba_get_rhill": (c_int, [vp, vp]),
             "symba_pool_get_rhill": (c_int, [vp, c_int, vp]),
+            "symba_measure_rates": (c_int, [dp]),
+            "symba_pool_enc_groups": (c_int, [vp, c_int, vp, vp, c_int, ip, ip]),
+            "symba_pool_set_state": (c_int, [vp, c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -324,6 +328,24 @@ class Pool:
         _check(lib().symba_pool_get_stats(self._h, int(slot), byref(s)), "symba_pool_get_stats")
         return s
 
+    def set_state(self, slot: int, x, v_bary) -> None:
+        """Replaces one system's positions (heliocentric) and barycentric velocities."""
+        xs, vs = _host(x, np.float64, (-1, 3)), _host(v_bary, np.float64, (-1, 3))
+        _check(lib().symba_pool_set_state(self._h, int(slot), _ptr(xs), _ptr(vs)), "symba_pool_set_state")
+
+    def enc_groups(self, slot: int, cap: int | None = None):
+        """Level-0 pairs of the system's last step, their groups and the group count."""
+        npairs, ngroups = c_int(), c_int()
+        _check(lib().symba_pool_enc_groups(self._h, int(slot), None, None, 0, byref(npairs), byref(ngroups)),
+               "symba_pool_enc_groups")
+        cap = npairs.value if cap is None else cap
+        pairs = np.zeros((max(cap, 1), 2), dtype=np.int32)
+        gop = np.zeros(max(cap, 1), dtype=np.int32)
+        _check(lib().symba_pool_enc_groups(self._h, int(slot), _ptr(pairs), _ptr(gop), cap, byref(npairs),
+                                           byref(ngroups)), "symba_pool_enc_groups")
+        k = min(cap, npairs.value)
+        return pairs[:k].copy(), gop[:k].copy(), ngroups.value
+
     def rhill(self, slot: int) -> np.ndarray:
         rh = np.zeros(self.n[slot])
         _check(lib().symba_pool_get_rhill(self._h, int(slot), _ptr(rh)), "symba_pool_get_rhill")
@@ -371,6 +393,18 @@ def step_many(systems, nsteps: int = 1) -> int:
     flight, so that none waits for a slower one (symba_step_many); waits for all."""
     arr = (c_void_p * len(systems))(*[s._h for s in systems])
     return _check(lib().symba_step_many(arr, len(systems), int(nsteps)), "symba_step_many")
+
+
+SYMBA_NRATES = 6
+
+
+def measure_rates() -> dict:
+    """The device rates that bound this path, measured now (symba_measure_rates)."""
+    out = (c_double * SYMBA_NRATES)()
+    _check(lib().symba_measure_rates(out), "symba_measure_rates")
+    v = list(out)
+    return {"fp64_flops": v[0], "warp_dfma_dep_cycles": v[1], "warp_dfma_4chain_cycles": v[2],
+            "named_barrier_round_trip_cycles": v[3], "sms": int(v[4]), "sm_clock_hz_nominal": v[5]}
 
 
 def G_default() -> float:

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsymba.so")
-SOURCES = ["api.cu", "k_misc.cu", "k_trap.cu", "k_groups.cu", "k_recur.cu", "k_static.cu", "k_tune.cu"]
+SOURCES = ["api.cu", "k_misc.cu", "k_trap.cu", "k_groups.cu", "k_recur.cu", "k_static.cu", "k_tune.cu",
+           "k_probe.cu"]
 HEADERS = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "ptr_class.h"),
            os.path.join(os.path.dirname(HERE), "include", "symba.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1019,6 +1019,15 @@ int symba_get_rhill(symba_ctx *c, double *rhill) {
 
 int symba_pool_get_rhill(symba_pool *pool, int slot, double *rhill) { return get_rhill(pool, slot, rhill); }
 
+int symba_pool_set_state(symba_pool *pool, int slot, const double *x, const double *v) {
+  return set_state(pool, slot, x, v);
+}
+
+int symba_pool_enc_groups(symba_pool *pool, int slot, int *pairs, int *group_of_pair, int cap, int *n_pairs,
+                          int *n_groups) {
+  return enc_groups(pool, slot, pairs, group_of_pair, cap, n_pairs, n_groups);
+}
+
 int symba_set_state(symba_ctx *c, const double *x, const double *v) {
   if (!c) return SYMBA_E_INVAL;
   return set_state(c->pool, c->slot, x, v);

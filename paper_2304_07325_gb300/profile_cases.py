@@ -5,6 +5,10 @@
     python -m paper_2304_07325_gb300.profile_cases bound_pair [--steps 1]
         one step of a 5-body encounter group of the 10,000-body disk (seed 1002) that holds a
         bound pair: the group recursion (k_recursion) dominates, ~34,000 sub-steps per step
+    python -m paper_2304_07325_gb300.profile_cases steps --n 10000 --steps 4
+        the disk stepped one call per step, with each step's recursion sub-steps split by path
+        (single-pair / general) -- beside an ncu count of FP64 instructions per k_recursion
+        launch, the FP64 instructions per sub-step of each path follow by least squares
 
 Each case prints the per-phase device times measured with CUDA events (symba_profile_step).
 """
@@ -19,7 +23,7 @@ BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["step", "bound_pair"])
+    ap.add_argument("case", choices=["step", "bound_pair", "steps"])
     ap.add_argument("--n", type=int, default=10000)
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--steps", type=int, default=1)
@@ -32,6 +36,16 @@ def main(argv=None):
         s = System(d.x[g], d.v[g], d.m[g], d.radius[g], params=default_params(precision=prec))
     else:
         s = System(d.x, d.v, d.m, d.radius, params=default_params(precision=prec))
+    if a.case == "steps":
+        print("step substeps pair_substeps general_substeps max_chain recursion_ms")
+        status = 0
+        for k in range(a.steps):
+            ph = s.profile_step(1)
+            st = s.stats()
+            status = s.sync()
+            print(f"{k} {st.substeps} {st.pair_substeps} {st.substeps - st.pair_substeps} {st.max_chain} {ph[5]:.3f}")
+        s.close()
+        return 0 if status >= 0 else 1
     ph = s.profile_step(a.steps)
     st = s.stats()
     status = s.sync()

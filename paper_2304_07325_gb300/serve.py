@@ -48,6 +48,7 @@ class Result:
     alive: np.ndarray = None
     energy: tuple = None
     status: int = 0
+    merges: int = 0
 
 
 @dataclass
@@ -125,7 +126,8 @@ class Server:
         if keep_state:
             res.x, res.v, _, _, res.alive = self.pool.get_state(slot)
             res.energy = self.pool.energy(slot)
-        res.status = self.pool.stats(slot).status
+        st = self.pool.stats(slot)
+        res.status, res.merges = st.status, int(st.merges)
         self.pool.evict(slot)
         n = len(req.m)
         self.used_particles -= 32 * ((n + 31) // 32)
@@ -220,7 +222,8 @@ class ConcurrentServer:
         if keep_state:
             res.x, res.v, _, _, res.alive = pool.get_state(ps)
             res.energy = pool.energy(ps)
-        res.status = pool.stats(ps).status
+        st = pool.stats(ps)
+        res.status, res.merges = st.status, int(st.merges)
         pool.evict(ps)
         self.free.append(k)
         return res
@@ -277,9 +280,10 @@ class ConcurrentServer:
 
 def poisson_requests(count: int, rate_per_s: float = 20.0, seed: int = 3000, n_lo: int = 500,
                      n_hi: int = 20000, steps_lo: int = 100, steps_hi: int = 5000, n_cap: int | None = None,
-                     steps_cap: int | None = None):
+                     steps_cap: int | None = None, params=None):
     """The served workload: Poisson arrivals, N log-uniform, step budgets uniform (optionally
-    capped for a bounded run)."""
+    capped for a bounded run); `params` (a symba_params, e.g. a step size and precision) applies
+    to every request (None: the defaults)."""
     from . import disk
     out = []
     for k, (t, n, steps, s) in enumerate(disk.request_stream(count, rate_per_s, seed, n_lo, n_hi, steps_lo, steps_hi)):
@@ -288,5 +292,6 @@ def poisson_requests(count: int, rate_per_s: float = 20.0, seed: int = 3000, n_l
         if steps_cap is not None:
             steps = min(steps, steps_cap)
         d = disk.planetesimal_disk(n, s)
-        out.append(Request(rid=k, arrival_s=t, x=d.x, v=d.v, m=d.m, radius=d.radius, n_massive=d.n_massive, steps=steps))
+        out.append(Request(rid=k, arrival_s=t, x=d.x, v=d.v, m=d.m, radius=d.radius, n_massive=d.n_massive, steps=steps,
+                           params=params))
     return out

@@ -28,6 +28,14 @@ def test_reference_line():
     assert line["value"] > 0 and line["higher_is_better"] is True and line["n_gpus"] == 1
     assert line["dtype"] == "f64" and line["data"] == "synthetic"
     assert "N_m=200" in line["config"]["workload"]
+    # the GPU arm's window: the same warm-up steps untimed, then exactly the timed steps, and the
+    # same workload string
+    assert line["steps"] == 2 and line["warmup"] == 3
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    ns = argparse.Namespace(n=200, n_field=0, precision="fp64", seed=1002)
+    assert line["config"]["workload"] == bench.workload_name(ns)
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert cb["unit"] == "pair-interactions/s" and cb["sample"]

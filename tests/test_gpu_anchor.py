@@ -1,0 +1,136 @@
+"""Pools, served requests and the mixed-precision kick against the oracle (needs a GB300).
+
+The other pool and serving tests compare the CUDA path with itself (a system in a pool or in the
+server equals the same system alone).  Here each pooled or served system is compared with its
+own run of the oracle: level-0 encounter pairs and groups bit for bit at every step, positions to
+1e-12 relative with the chaos-aware allowance (100x the spread of the oracle's sensitivity twin),
+and the massive/field split of Sec. 2 in mixed precision against the FP64 oracle with the error
+stated per result.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from paper_2304_07325_gb300 import disk  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sy():
+    import paper_2304_07325_gb300 as m
+    from paper_2304_07325_gb300 import build
+    build.build()
+    return m
+
+
+def _twin_of(orc, d, ref):
+    """The oracle with rounding-level perturbations at every recursion sub-step, from ref's state."""
+    tw = orc.OracleSim(d.x, d.v, d.m, d.radius, n_massive=d.n_massive, rhill=ref.rhill,
+                       params=orc.make_params(noise=1))
+    tw.set_state(ref.x, ref.v)
+    for a in ("alive", "m", "radius", "rhill"):
+        getattr(tw, a)[...] = getattr(ref, a)
+    return tw
+
+
+def _chaos_aware(x, ref, twin, tol=1e-12, factor=100.0):
+    norm = np.linalg.norm(ref.x, axis=1)
+    rel = np.linalg.norm(x - ref.x, axis=1) / norm
+    spread = np.linalg.norm(twin.x - ref.x, axis=1) / norm
+    bad = np.where(rel > np.maximum(tol, factor * spread))[0]
+    assert len(bad) == 0, [(int(i), rel[i], spread[i]) for i in bad[:5]]
+    return rel
+
+
+def test_pool_systems_match_their_oracles(orc, sy):
+    """Four uneven disks (one with field particles) in one pool, three steps: every system's
+    encounter pairs and groups equal its own oracle's at every step; each step starts the pooled
+    system from its oracle's state, so positions are compared one step at a time (1e-12,
+    chaos-aware)."""
+    specs = [(1000, 0, 2000), (333, 0, 2001), (2049, 0, 2002), (200, 800, 2003)]
+    disks = [disk.planetesimal_disk(n, s, n_field=nf) for n, nf, s in specs]
+    tiles = sum(((d.n + 31) // 32) * ((d.n_massive + 31) // 32) for d in disks)
+    pool = sy.Pool(8, sum(d.n for d in disks) + 1024, tiles)
+    slots = [pool.admit(d.x, d.v, d.m, d.radius, n_massive=d.n_massive) for d in disks]
+    refs = [orc.OracleSim(d.x, d.v, d.m, d.radius, n_massive=d.n_massive) for d in disks]
+    for s, ref in zip(slots, refs):
+        assert np.array_equal(pool.rhill(s), ref.rhill)
+    npairs = 0
+    for step in range(3):
+        # every step starts the pool's systems from their oracles' states: one-step comparisons
+        for s, ref in zip(slots, refs):
+            pool.set_state(s, ref.x, ref.v)
+        twins = [_twin_of(orc, d, ref) for d, ref in zip(disks, refs)]
+        pool.step(1)
+        assert pool.sync() >= 0
+        for d, s, ref, tw in zip(disks, slots, refs, twins):
+            assert ref.step(1) >= 0 and tw.step(1) >= 0
+            p_ref, g_ref, ng_ref = ref.enc_groups()
+            p_gpu, g_gpu, ng_gpu = pool.enc_groups(s)
+            assert ng_gpu == ng_ref and np.array_equal(p_gpu, p_ref) and np.array_equal(g_gpu, g_ref), (d.label, step)
+            npairs += len(p_ref)
+            x, v, m, r, a = pool.get_state(s)
+            assert np.array_equal(a, ref.alive) and np.array_equal(m, ref.m)
+            assert np.array_equal(r, ref.radius) and np.array_equal(pool.rhill(s), ref.rhill)
+            _chaos_aware(x, ref, tw)
+    assert npairs > 30
+    pool.close()
+
+
+def test_served_request_matches_the_oracle(orc, sy):
+    """Requests served by the continuous-batching server (mixed with others on the device): each
+    final state against the oracle run for the same number of steps -- survivors bit-exact,
+    positions 1e-12 chaos-aware, energy to 1e-12 relative."""
+    from paper_2304_07325_gb300.serve import Server, poisson_requests
+    reqs = poisson_requests(4, rate_per_s=200.0, seed=3300, n_lo=200, n_hi=1200, steps_lo=2, steps_hi=4)
+    srv = Server(max_systems=3, max_particles=3 * 1280, max_tiles=3 * 40 * 41 // 2)
+    results, stats = srv.run(reqs)
+    srv.close()
+    assert stats.max_resident >= 2 and len(results) == 4
+    for res in results:
+        req = reqs[res.rid]
+        d = disk.Disk(x=req.x, v=req.v, m=req.m, radius=req.radius, n_massive=req.n_massive, seed=0, label="")
+        ref = orc.OracleSim(req.x, req.v, req.m, req.radius, n_massive=req.n_massive)
+        tw = _twin_of(orc, d, ref)
+        for _ in range(req.steps):
+            assert ref.step(1) >= 0 and tw.step(1) >= 0
+        assert res.steps == req.steps and res.status == 0
+        assert np.array_equal(res.alive, ref.alive)
+        _chaos_aware(res.x, ref, tw)
+        E_ref, _ = ref.energy()
+        assert abs(res.energy[0] - E_ref) <= 1e-12 * abs(E_ref), (res.energy[0], E_ref)
+
+
+def test_mixed_and_fp64_against_the_oracle_massive_field_split(orc, sy):
+    """Sec. 2's massive/field classes at 1,000 massive + 10,000 field particles (seed 1003; the
+    benchmark's field-dominated shape at a tenth of its field count so that the oracle runs in
+    seconds): 10 steps of the FP64 and the mixed-precision path against the FP64 oracle.  Stated
+    per result: relative energy error of each and its difference from the oracle's; median, p99
+    and max relative position error against the oracle."""
+    d = disk.planetesimal_disk(1000, 1003, n_field=10000)
+    steps = 10
+    ref = orc.OracleSim(d.x, d.v, d.m, d.radius, n_massive=1000)
+    E0, _ = ref.energy()
+    assert ref.step(steps) >= 0
+    E_ref, _ = ref.energy()
+    out = {}
+    for name, prec in (("fp64", sy.SYMBA_PRECISION_FP64), ("mixed", sy.SYMBA_PRECISION_MIXED)):
+        s = sy.System(d.x, d.v, d.m, d.radius, n_massive=1000, params=sy.default_params(precision=prec))
+        s.step(steps)
+        assert s.sync() >= 0
+        x, *_ = s.get_state()
+        E, _ = s.energy()
+        rel = np.linalg.norm(x - ref.x, axis=1) / np.linalg.norm(ref.x, axis=1)
+        out[name] = {"dE": abs((E - E0) / E0), "dE_vs_oracle": abs((E - E_ref) / E0),
+                     "p50": float(np.median(rel)), "p99": float(np.percentile(rel, 99)), "max": float(rel.max())}
+        s.close()
+    print(f"oracle dE {abs((E_ref - E0) / E0):.3e}; " +
+          "; ".join(f"{k}: " + ", ".join(f"{a} {b:.2e}" for a, b in v.items()) for k, v in out.items()))
+    # FP64 path: rounding-level agreement with the oracle for all but chaotic bodies
+    assert out["fp64"]["p50"] < 1e-14 and out["fp64"]["p99"] < 1e-12
+    assert out["fp64"]["dE_vs_oracle"] < 1e-13
+    # mixed: FP32 pair forces (relative error ~1e-7 of forces that move bodies by ~1e-7 of their
+    # orbit per step) leave positions within 1e-10 for almost every body; the energy is the
+    # integrator's, changed far below its own error
+    assert out["mixed"]["p50"] < 1e-11 and out["mixed"]["p99"] < 1e-9
+    assert out["mixed"]["dE_vs_oracle"] < 1e-11

@@ -7,6 +7,7 @@ from paper_2304_07325_gb300.serve import Request, Server
 
 class FakeStats:
     status = 0
+    merges = 0
 
 
 class FakePool:
