@@ -39,7 +39,7 @@ FP64_PER_GENERAL_SUBSTEP = 933.0
 BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
 # DRAM read + write per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, N = 10,000, FP64)
 # of the current kernels; None until a capture of the current kernel is on record
-RECURSION_TRAFFIC_BYTES = None
+RECURSION_TRAFFIC_BYTES = 2305280 + 20480      # first step of the disk (profiles/launches_bench_disk_N10000.md)
 KICK_TRAFFIC_BYTES = None
 # Step size at which the batched and served forms and the one-at-a-time form all keep the energy
 # error of every merger-free disk below 1e-10 (measured on the 64 batched disks: 5.7e-11 after 20
@@ -79,8 +79,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true",
                     help="single mode: skip the served Poisson stream at matched accuracy")
     ap.add_argument("--batched-steps", type=int, default=20)
-    ap.add_argument("--served-requests", type=int, default=24)
-    ap.add_argument("--served-steps-cap", type=int, default=40)
+    ap.add_argument("--served-requests", type=int, default=16)
+    ap.add_argument("--served-steps-cap", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched mode: keep the default launch schedule instead of autotuning it")
     return ap.parse_args()
@@ -401,7 +401,7 @@ def bench_batched(sy, disk, steps, warmup, serial_steps):
     return out
 
 
-def bench_served(sy, count, steps_cap, serial_steps):
+def bench_served(sy, count, steps_cap):
     """Config-5 shape: Poisson arrivals (20/s), N log-uniform 500-20,000, step budgets U[100, 5000]
     capped for a bounded run, mixed-precision kick, served by the concurrent server (resident
     single-system pools, one stream each, one step in flight per request) at the matched-accuracy
@@ -423,15 +423,15 @@ def bench_served(sy, count, steps_cap, serial_steps):
         s0.close()
         E1.append(res.energy[0])
         merges.append(res.merges)
+    # the same requests one at a time, FP64, each for its whole (capped) budget: the same work
     t_serial, n_serial = 0.0, 0
     for r in reqs:
         s1 = sy.System(r.x, r.v, r.m, r.radius, n_massive=r.n_massive, params=sy.default_params(dt=MATCHED_TAU))
-        k = min(serial_steps, r.steps)
         t0 = time.perf_counter()
-        s1.step(k)
+        s1.step(r.steps)
         s1.sync()
         t_serial += time.perf_counter() - t0
-        n_serial += k
+        n_serial += r.steps
         s1.close()
     serial = n_serial / t_serial
     return {"workload": f"{count} Poisson requests (20/s), N log-uniform 500-20,000, step budgets U[100,5000] "
@@ -442,7 +442,8 @@ def bench_served(sy, count, steps_cap, serial_steps):
             "step_latency": "per request step, launch to observed completion", "wall_s": summ["wall_s"],
             "max_resident": summ["max_resident"], "energy_error": _energy_errors(E0, E1, merges),
             "one_at_a_time_fp64": {"value": serial, "unit": "sim-steps/s",
-                                   "sample": f"the first min({serial_steps}, budget) steps of each request alone"},
+                                   "sample": "every request alone for its whole capped budget, FP64, one after "
+                                             "another (the same sim-steps as the served run)"},
             "speedup_vs_one_at_a_time_fp64": summ["sim_steps_per_s"] / serial}
 
 
@@ -623,9 +624,9 @@ def run_ours(args):
         chain = chain_vs_cpu(sy, disk) if world == 1 and not args.no_cpu_baseline else None
         # spec target 2: batched and served forms against one simulation per launch
         # sequence, FP64, at a step size where every form keeps the energy error <= 1e-10
-        batched = None if args.no_batched or world > 1 else bench_batched(sy, disk, args.batched_steps, 2, 3)
+        batched = None if args.no_batched or world > 1 else bench_batched(sy, disk, args.batched_steps, 1, 2)
         served = None if args.no_served or world > 1 else bench_served(sy, args.served_requests,
-                                                                          args.served_steps_cap, 3)
+                                                                          args.served_steps_cap)
         line = {"metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -862,6 +863,9 @@ def run_field(args):
 
 def main():
     args = parse()
+    # one hardware work queue per stream for the concurrently stepped contexts of the batched and
+    # served forms (read when the CUDA context is created, so before the first CUDA call)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batched":

@@ -94,36 +94,59 @@ __device__ __forceinline__ void set_status(DiskStat *st, int code) {
 
 __device__ __forceinline__ int find_disk(const int *blk_disk, int p) { return blk_disk[p >> 5]; }
 
-// r^-3 for the pair kick: seed 1/sqrt(r2) from the top 23 mantissa bits of r2 with one MUFU
-// rsqrt (exponent re-biased with integer operations, so no FP64 conversion is issued), then the
-// third-order correction r^-3 = y0^3 (1 - e)^{-3/2} ~ y0^3 (1 + 3/2 e + 15/8 e^2),
-// e = 1 - r2 y0^2 (|e| < 2^-19, truncation < 2^-57): 5 FP64 instructions.  Values of r2 outside
-// the normal FP32 range take the library path.
+// The double nearest M 2^e2 (M > 0; ties away from zero), built on the integer pipe: normalise,
+// keep 53 bits, add the rounding bit; adding the 53-bit significand (hidden bit included) to
+// (exponent - 1) << 52 carries into the exponent field by itself.  Normal results only.
+__device__ __forceinline__ double u64_scaled(unsigned long long M, int e2) {
+  const int lz = __clzll(M);
+  const unsigned long long n = M << lz;                       // top bit at 63
+  const unsigned long long m = (n >> 11) + ((n >> 10) & 1ull);  // in [2^52, 2^53]
+  const long long ex = (long long)(e2 - lz + 63 + 1022);
+  return __longlong_as_double((long long)(((unsigned long long)ex << 52) + m));
+}
+
+// r^-3 for the pair kick with two FP64 instructions (the kick is bound by the FP64 pipe, so the
+// rest of the work goes to the integer pipe and one MUFU operation):
+//   seed     y0 = Y 2^ye (Y a 24-bit integer) from one MUFU rsqrt of the top 24 bits of r2,
+//            |1 - r2 y0^2| < 2^-21;
+//   Newton   one step in 64-bit integers: D = 2^k (1 - r2 y0^2) from the high word of R Y^2 (R
+//            the 53-bit significand of r2), y1 = y0 (1 + (1 - r2 y0^2) / 2) kept as a ~40-bit
+//            integer Y1 (|1 - r2 y1^2| < 2^-37);
+//   powers   t = RN(y1^2), c = RN(y1^3), c15 = RN(3/2 y1^3) from Y1 on the integer pipe;
+//   finish   e = 1 - r2 t (one FMA), r^-3 = y1^3 (1 - e)^{-3/2} = c + c15 e (one FMA; the next
+//            term 15/8 e^2 < 2^-72 is far below the rounding).
+// Error below 1.7 x 2^-52 relative (y1's quantisation enters only through e; t, c and the two
+// FMAs round once each).  Values of r2 outside the normal FP32 range take the library path.
 __device__ __forceinline__ double rinv3(double r2) {
-  const int hi = __double2hiint(r2);
-  const unsigned lo = (unsigned)__double2loint(r2);
-  const int fe = ((hi >> 20) & 0x7FF) - 896;
-  if ((unsigned)(fe - 1) <= 253u && hi > 0) {
-    const unsigned m23 = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(r2);
+  const int E = (int)(rb >> 52) & 0x7FF;
+  const int fe = E - 896;
+  if ((unsigned)(fe - 1) <= 253u && (long long)rb > 0) {
+    const unsigned m23 = (unsigned)(rb >> 29) & 0x7FFFFFu;
     const float r2f = __uint_as_float(((unsigned)fe << 23) | m23);
     float y0f;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(r2f));
     const unsigned yb = __float_as_uint(y0f);
-    const int ye = (int)((yb >> 23) & 0xFF) + 896;
-    const double y0 = __hiloint2double((ye << 20) | (int)((yb & 0x7FFFFF) >> 3), (int)((yb & 7u) << 29));
-    // t = y0^2, exact (24 significant bits squared), built from the integer square of the
-    // mantissa so that no FP64 instruction is spent on it
-    const unsigned long long my = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u);
-    const unsigned long long sq = my * my;                 // in [2^46, 2^48)
-    const int top = (int)(sq >> 47);
-    const long long te = 2 * (ye - 1023) + top + 1023;
-    const double t = __longlong_as_double((long long)(((unsigned long long)te << 52) |
-                                                      ((sq << (6 - top)) & 0xFFFFFFFFFFFFFull)));
-    const double y03 = t * y0;
+    const long long Y = (long long)((yb & 0x7FFFFFu) | 0x800000u);
+    const int ye = (int)((yb >> 23) & 0xFFu) - 150;                        // y0 = Y 2^ye
+    const unsigned long long R = (rb & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // r2 = R 2^(E-1075)
+    const unsigned long long H = __umul64hi(R << 11, (unsigned long long)(Y * Y) << 16);
+    const int k = 1038 - E - 2 * ye;                  // R Y^2 2^-37 = H ~ 2^k, k in 61..64
+    // D = 2^k - H, |D| < 2^(k-20); for k = 64 the unsigned difference wraps to 2^64 - H
+    const long long D = (long long)((k < 64 ? (1ull << (k & 63)) : 0ull) - H);
+    const long long Dp = k <= 63 ? (D << ((63 - k) & 63)) : (D >> 1);       // D 2^(63-k)
+    const long long C = __mul64hi(Y << 16, Dp << 16) >> 16;                  // Y D' 2^-48
+    const unsigned long long Y1 = (unsigned long long)((Y << 16) + C);       // y1 = Y1 2^(ye-16)
+    const int sh = __clzll(Y1);
+    const unsigned long long N = Y1 << sh;                                    // y1 = N 2^(ye-16-sh)
+    const int ne = ye - 16 - sh;
+    const unsigned long long Q = __umul64hi(N, N);                            // N^2 2^-64
+    const unsigned long long QN = __umul64hi(Q, N);                           // N^3 2^-128
+    const double t = u64_scaled(Q, 2 * ne + 64);
+    const double c = u64_scaled(QN, 3 * ne + 128);
+    const double c15 = u64_scaled(3ull * (QN >> 2), 3 * ne + 129);
     const double e = fma(-r2, t, 1.0);
-    const double p = fma(e, 1.875, 1.5);
-    const double ep = e * p;
-    return fma(y03, ep, y03);
+    return fma(e, c15, c);
   }
   const double y = rsqrt(r2);
   return y * y * y;

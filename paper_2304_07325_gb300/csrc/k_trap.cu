@@ -14,8 +14,9 @@
 // and summed later in a fixed order: the result does not depend on scheduling, segment length
 // or which other systems share the launch.
 //
-// FP64 path: 20 FP64-pipe instructions per pair (3 differences, 3 for r^2, 6 for r^-3 from an
-// integer-built FP32 seed, 2 mass scalings, 6 FMAs into the two accumulators).
+// FP64 path: 16 FP64-pipe instructions per pair (3 differences, 3 for r^2, 2 for r^-3 -- its seed,
+// Newton step and powers run on the integer pipe -- 2 mass scalings, 6 FMAs into the two
+// accumulators).
 //
 // Kick 1 also runs the close-encounter check (Sec. 2) of every pair: a conservative FP32
 // prefilter (|d| - tau |dv| against R_0 with rounding margins) and, for the rare pairs that pass,
