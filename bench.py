@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--served-requests", type=int, default=16)
     ap.add_argument("--served-steps-cap", type=int, default=10)
+    ap.add_argument("--oracle-steps", type=int, default=50,
+                    help="field mode: steps of the FP64 oracle (host, in parallel) the GPU paths are compared with")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched mode: keep the default launch schedule instead of autotuning it")
     return ap.parse_args()
@@ -804,11 +806,36 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_field_run(nm, nf, seed, steps, conn):
+    """Child process (spawned): the oracle on the field-dominated disk for `steps` steps."""
+    import oracle
+    from paper_2304_07325_gb300 import disk
+    d = disk.planetesimal_disk(nm, seed, n_field=nf)
+    sim = oracle.OracleSim(d.x, d.v, d.m, d.radius, n_massive=nm)
+    E0, _ = sim.energy()
+    t0 = time.perf_counter()
+    st = sim.step(steps)
+    el = time.perf_counter() - t0
+    E1, _ = sim.energy()
+    conn.send({"status": st, "x": sim.x.copy(), "E0": E0, "E1": E1, "seconds": el, "alive": sim.alive.copy()})
+    conn.close()
+
+
 def run_field(args):
-    """Field-particle-dominated disk (N_m massive + n_field massless; default 1,000 + 100,000):
-    the mixed-precision path (FP32 pair math, FP64 state) timed per step, and its accuracy after
-    the same number of steps against the FP64 path from the same input (energy error of each,
-    largest relative position difference).  Metric: pair interactions per second."""
+    """Field-particle-dominated disk (N_m massive + n_field massless; default 1,000 + 100,000,
+    seed 1003): the mixed-precision path (FP32 pair math, FP64 state) and the FP64 path timed per
+    step over `steps` steps, the error of both against the FP64 oracle after `--oracle-steps`
+    steps (the oracle runs meanwhile in a spawned process on the host), and mixed against FP64
+    after all steps.  Metric: pair interactions per second of the mixed path."""
+    import multiprocessing as mp
+    nm, nf = args.n, args.n_field if args.n_field > 0 else 100000
+    ko = max(0, args.oracle_steps)
+    child, conn = None, None
+    if ko > 0:
+        ctx = mp.get_context("spawn")          # started before the first CUDA call
+        conn, child_conn = ctx.Pipe(duplex=False)
+        child = ctx.Process(target=_oracle_field_run, args=(nm, nf, 1003, ko, child_conn))
+        child.start()
     import torch
 
     import paper_2304_07325_gb300 as sy
@@ -816,20 +843,22 @@ def run_field(args):
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    nm, nf = args.n, args.n_field if args.n_field > 0 else 100000
+    rates = sy.measure_rates()
     d = disk.planetesimal_disk(nm, 1003, n_field=nf)
     P = nm * (nm - 1) // 2 + nm * nf
-    out = {}
+    out, snap = {}, {}
     for name, prec in (("mixed", sy.SYMBA_PRECISION_MIXED), ("fp64", sy.SYMBA_PRECISION_FP64)):
         s = sy.System(d.x, d.v, d.m, d.radius, n_massive=nm, params=sy.default_params(precision=prec))
         E0, _ = s.energy()
-        s.profile_step(max(1, args.warmup))
         clocks = ClockSampler(0)
         torch.cuda.synchronize()
         clocks.start()
         ph = np.zeros(sy.SYMBA_NPHASES)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for k in range(args.steps):
+            if k == ko and ko > 0:
+                xk, *_ = s.get_state()
+                snap[name] = (xk, s.energy()[0])
             ph += s.profile_step(1)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -839,25 +868,47 @@ def run_field(args):
             raise RuntimeError(f"{name}: {sy.status_string(st)}")
         E1, _ = s.energy()
         x, *_ = s.get_state()
+        if ko > 0 and name not in snap:
+            snap[name] = (x, E1)
         dev_ms = float(ph.sum())
+        kick_ms = float(ph[1] + ph[6]) / (2 * args.steps)
         out[name] = {"ms_per_step": dev_ms / args.steps, "pairs_per_s": 2.0 * P * args.steps / (dev_ms * 1e-3),
-                     "dE_rel": abs((E1 - E0) / E0), "x": x, "clocks": clk, "wall_s": wall,
-                     "kick_ms": float(ph[1] + ph[6]) / (2 * args.steps)}
+                     "dE_rel": abs((E1 - E0) / E0), "x": x, "E0": E0, "clocks": clk, "wall_s": wall,
+                     "kick_ms": kick_ms, "recursion_ms_per_step": float(ph[5]) / args.steps,
+                     "kick_tflops": FLOPS_PER_PAIR_KICK * P / (kick_ms * 1e-3) / 1e12}
         s.close()
     xm, xd = out["mixed"].pop("x"), out["fp64"].pop("x")
-    rel = np.linalg.norm(xm - xd, axis=1) / np.linalg.norm(xd, axis=1)
-    dx = {"p50": float(np.percentile(rel, 50)), "p99": float(np.percentile(rel, 99)),
-          "max": float(rel.max()), "frac_below_1e-10": float(np.mean(rel < 1e-10)),
-          "note": "close encounters amplify rounding differences; the tail is chaotic divergence"}
+
+    def rel_err(a, b):
+        r = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+        return {"p50": float(np.percentile(r, 50)), "p99": float(np.percentile(r, 99)), "max": float(r.max()),
+                "frac_below_1e-12": float(np.mean(r < 1e-12))}
+
+    vs_oracle = None
+    if child is not None:
+        res = conn.recv()
+        child.join()
+        vs_oracle = {"steps": ko, "oracle_seconds": res["seconds"], "oracle_status": res["status"],
+                     "oracle_dE_rel": abs((res["E1"] - res["E0"]) / res["E0"])}
+        for name in ("mixed", "fp64"):
+            xk, Ek = snap[name]
+            E0 = out[name]["E0"]
+            vs_oracle[name] = {"dE_rel": abs((Ek - E0) / E0), "dE_minus_oracle": abs((Ek - res["E1"]) / E0),
+                               "position_rel_err": rel_err(xk, res["x"])}
+    for name in ("mixed", "fp64"):
+        out[name].pop("E0")
     m = out["mixed"]
     line = {"metric": "pair-interactions/s", "value": m["pairs_per_s"], "unit": "pair-interactions/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+            "n_gpus": 1, "steps": args.steps, "warmup": 0, "ms_per_step": m["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-pair/f64-state", "data": "synthetic",
             "config": {"workload": f"field-dominated disk N_m={nm} + {nf} massless (seed 1003), dt=0.5 yr, "
                                    "M=4, R_k/R_k+1=2.08, l=3", "pairs_per_kick": P, "l2": "inputs > L2"},
-            "mixed": m, "fp64": out["fp64"],
-            "rel_dx_mixed_vs_fp64": dx, "clocks": m["clocks"]}
+            "mixed": m, "fp64": out["fp64"], "rates": rates,
+            "rel_dx_mixed_vs_fp64": dict(rel_err(xm, xd), after_steps=args.steps,
+                                         note="close encounters amplify rounding differences; the tail "
+                                              "is chaotic divergence"),
+            "vs_oracle": vs_oracle, "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
 
 

@@ -49,11 +49,9 @@ struct RangeAlloc {
   }
 };
 
-long long tiles_of(int nb, int nbm) {
-  long long t = 0;
-  for (int I = 0; I < nbm; ++I) t += nb - I;
-  return t;
-}
+// trapezoid tiles of a system: (I, J), I <= J, over the column blocks that hold massive bodies
+// (blocks of field particles only are rows of the field rectangle instead)
+long long tiles_of(int nbm) { return (long long)nbm * (nbm + 1) / 2; }
 
 int default_pair_cap(const symba_params *p, int n) {
   if (p && p->pair_capacity > 0) return p->pair_capacity;
@@ -158,6 +156,7 @@ int rebuild(symba_pool *P) {
     phw = std::max(phw, (long long)s.off + (long long)s.nb * SYM_TILE);
   }
   std::vector<DiskDesc> descs(P->max_disks);
+  std::vector<int2> fblk;
   bool any_discard = false;
   for (int d = 0; d < P->max_disks; ++d) {
     Slot &s = P->slots[d];
@@ -179,7 +178,8 @@ int rebuild(symba_pool *P) {
     any_discard = any_discard || dd.rmin2 > 0.0 || dd.rmax2 > 0.0;
     const int b0 = s.off / SYM_TILE;
     for (int I = 0; I < s.nbm; ++I)
-      for (int J = I; J < s.nb; ++J) tiles.push_back(make_int4(d, b0 + I, b0 + J, 0));
+      for (int J = I; J < s.nbm; ++J) tiles.push_back(make_int4(d, b0 + I, b0 + J, 0));
+    for (int B = s.nbm; B < s.nb; ++B) fblk.push_back(make_int2(d, b0 + B));
   }
   P->ndisks = hw;
   P->npart_hwm = phw;
@@ -191,6 +191,9 @@ int rebuild(symba_pool *P) {
   P->D.seg_len = P->seg_override > 0 ? P->seg_override : (int)std::max(1LL, std::min(8LL, seg));
   if (!tiles.empty())
     CK(cudaMemcpyAsync(P->D.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, P->stream));
+  P->D.nfblk = (int)fblk.size();
+  if (!fblk.empty())
+    CK(cudaMemcpyAsync(P->D.fblk, fblk.data(), fblk.size() * sizeof(int2), cudaMemcpyHostToDevice, P->stream));
   // ck tables are filled on the device by the set-up kernel: keep them across uploads
   CK(cudaStreamSynchronize(P->stream));
   std::vector<DiskDesc> cur(P->max_disks);
@@ -212,6 +215,7 @@ void enqueue_step(symba_pool *P, cudaEvent_t rec0 = nullptr, cudaEvent_t rec1 = 
   launch_prologue(D, P->ndisks, P->stream);
   launch_sundrift(D, np, 1, P->stream);
   launch_trap(D, P->L, 1, P->precision, P->stream);
+  launch_field(D, 1, P->precision, P->stream);
   launch_reduce(D, np, P->precision, P->stream);
   launch_groups(D, P->ndisks, P->stream);
   if (P->group_order) launch_order_groups(D, P->stream);
@@ -221,6 +225,7 @@ void enqueue_step(symba_pool *P, cudaEvent_t rec0 = nullptr, cudaEvent_t rec1 = 
   if (rec1) cudaEventRecord(rec1, P->stream);
   if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, P->stream);
   launch_trap(D, P->L, 2, P->precision, P->stream);
+  launch_field(D, 2, P->precision, P->stream);
   launch_reduce(D, np, P->precision, P->stream);
   if (P->any_discard) launch_discard(D, np, P->stream);
   launch_momentum(D, P->ndisks, P->stream);
@@ -254,6 +259,7 @@ int pool_profile(symba_pool *P, int nsteps, double *phase_ms) {
     launch_sundrift(D, np, 1, s);
     cudaEventRecord(ev[1], s);
     launch_trap(D, P->L, 1, P->precision, s);
+    launch_field(D, 1, P->precision, s);
     cudaEventRecord(ev[2], s);
     launch_reduce(D, np, P->precision, s);
     cudaEventRecord(ev[3], s);
@@ -266,6 +272,7 @@ int pool_profile(symba_pool *P, int nsteps, double *phase_ms) {
     if (P->precision == SYMBA_PRECISION_MIXED) launch_split(D, np, s);
     cudaEventRecord(ev[6], s);
     launch_trap(D, P->L, 2, P->precision, s);
+    launch_field(D, 2, P->precision, s);
     cudaEventRecord(ev[7], s);
     launch_reduce(D, np, P->precision, s);
     if (P->any_discard) launch_discard(D, np, s);
@@ -357,6 +364,7 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   A(&D.disks, max_disks); A(&D.stat, max_disks); A(&D.P, 3 * max_disks);
   A(&D.sacc, (size_t)max_disks * 3 * (SA_NDIG + 1));
   A(&D.tiles, P->tcap);
+  A(&D.fblk, n / SYM_TILE + 1);
   A(&D.part, (size_t)P->tcap * 2 * 3 * 32);
   A(&D.work, 4);
   A(&D.raw_i, pc); A(&D.raw_j, pc); A(&D.pi, pc); A(&D.pj, pc); A(&D.gop, pc);
@@ -407,7 +415,7 @@ int pool_admit(symba_pool *P, const symba_params *p, int n, int nm, const double
   s.n = n; s.nm = nm; s.p = *p;
   s.nb = (n + SYM_TILE - 1) / SYM_TILE;
   s.nbm = (nm + SYM_TILE - 1) / SYM_TILE;
-  s.ntiles = (int)tiles_of(s.nb, s.nbm);
+  s.ntiles = (int)tiles_of(s.nbm);
   s.pair_cap = default_pair_cap(p, n);
   if (P->tiles_used + s.ntiles > P->tcap) return SYMBA_E_NOMEM;
   const long long po = P->parts.alloc((long long)s.nb * SYM_TILE);
@@ -824,7 +832,7 @@ long long symba_pool_footprint(int n, int n_massive, const symba_params *p) {
   const long long per_particle = 20 * 8 + 3 * 4 + 12 * 4 + 12 * 4 + 3 * 8 + 6 * 4 / 2 + 4;
   const long long pairs = default_pair_cap(p, n);
   const long long per_pair = 13 * 4 + 7 * 8 + 2 * 4;
-  return np * per_particle + pairs * per_pair + tiles_of((int)nb, (int)nbm) * (16 + 2 * 3 * 32 * 8);
+  return np * per_particle + pairs * per_pair + tiles_of((int)nbm) * (16 + 2 * 3 * 32 * 8) + 8 * nb;
 }
 
 int symba_pool_create(symba_pool **out, int max_systems, long long max_particles, long long max_tiles,
@@ -920,7 +928,7 @@ int symba_init(symba_ctx **out, const symba_params *p, int n, int n_massive, con
   *out = nullptr;
   symba_pool *P = nullptr;
   const long long nb = (n + SYM_TILE - 1) / SYM_TILE, nbm = (n_massive + SYM_TILE - 1) / SYM_TILE;
-  const long long tiles = std::max(1LL, tiles_of((int)nb, (int)nbm));
+  const long long tiles = std::max(1LL, tiles_of((int)nbm));
   int st = pool_create(&P, 1, n, tiles, default_pair_cap(p, n), p->precision, cuda_stream);
   if (st != SYMBA_OK) return st;
   int slot = -1;

@@ -6,6 +6,7 @@
 //   alive, gid                                     : int per particle (gid = encounter group or -1)
 //   xf, yf, zf, vxf, vyf, vzf, lamf, sigf          : FP32 copies for the encounter prefilter
 //   tiles                                          : int4 {system, I-block, J-block, 0} per 32x32 tile
+//   fblk                                           : int2 {system, block} per block of field particles
 //   part                                           : FP64 [tile][2 sides][3][32] pair-kick partials
 #pragma once
 #include <cuda_runtime.h>
@@ -54,8 +55,10 @@ struct Dev {
   double *P;                    // [max_disks][3] total barycentric momentum (for the sun drift)
   unsigned long long *sacc;     // [max_disks][3][SA_NDIG + 1] exact accumulators
   // trapezoid
-  int4 *tiles;
+  int4 *tiles;                  // tiles (I, J), I <= J < ceil(N_m / 32): column blocks holding massive bodies
   double *part;                 // [tile][2][3][32]
+  int2 *fblk;                   // field rectangle: {system, block} of every block of field particles only
+  int nfblk;
   int *work;                    // [4] dynamic work counters (kick 1, kick 2, recursion, spare)
   int ntiles_total;
   int seg_len;                  // tiles per work item
@@ -669,6 +672,7 @@ void launch_gather_state(const Dev &D, int d, int n, double *x, double *v, doubl
 void launch_scatter_state(const Dev &D, int d, int n, const double *x, const double *v,
                           cudaStream_t s);
 void launch_prologue(const Dev &D, int ndisks, cudaStream_t s);
+void launch_field(const Dev &D, int mode, int precision, cudaStream_t s);
 void launch_discard(const Dev &D, long long npart, cudaStream_t s);
 int trap_blocks_per_sm(int precision);
 int recursion_blocks_per_sm();

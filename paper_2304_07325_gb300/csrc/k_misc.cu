@@ -249,7 +249,7 @@ void launch_sundrift(const Dev &D, long long npart, int pre, cudaStream_t s) {
 // (I, B), I = 0..min(B, nbm)-1; the diagonal tile's column side is folded into its row side.
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ int row_start(const DiskDesc &dd, int I) {
-  return dd.tile_base + I * dd.nb - (I * (I - 1)) / 2;
+  return dd.tile_base + I * dd.nbm - (I * (I - 1)) / 2;
 }
 
 __global__ void k_reduce(Dev D, long long npart) {
@@ -262,9 +262,10 @@ __global__ void k_reduce(Dev D, long long npart) {
     const int li = (int)p - dd.off;
     if (li >= dd.n || !D.alive[p]) continue;
     const int B = li >> 5, lane = li & 31;
+    if (B >= dd.nbm) continue;                  // a block of field particles: kicked by k_field_*
     // the partials of p in a fixed order (its row, then its column), as a list of tile slots;
     // two interleaved sums (even and odd terms) keep two loads in flight, combined at the end
-    const int nrow = B < dd.nbm ? dd.nb - B : 0;
+    const int nrow = dd.nbm - B;
     const int Imax = B < dd.nbm ? B : dd.nbm;
     const int nterm = nrow + Imax;
     const int t0 = nrow ? row_start(dd, B) : 0;
@@ -312,10 +313,11 @@ __global__ void k_reduce_mixed(Dev D, long long npart) {
     const int li = (int)p - dd.off;
     if (li >= dd.n || !D.alive[p]) continue;
     const int B = li >> 5, lane = li & 31;
+    if (B >= dd.nbm) continue;                  // a block of field particles: kicked by k_field_mixed
     float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-    if (B < dd.nbm) {
+    {
       const int t0 = row_start(dd, B);
-      for (int J = B; J < dd.nb; ++J) {
+      for (int J = B; J < dd.nbm; ++J) {
         const float2 *pp = part + ((size_t)(t0 + (J - B)) * 2 * 3) * 32 + lane;
         for (int k = 0; k < 3; ++k) { kahan_add(s[k], c[k], pp[32 * k].x); kahan_add(s[k], c[k], -pp[32 * k].y); }
       }

@@ -389,3 +389,208 @@ void launch_trap(const Dev &D, const LaunchCfg &L, int mode, int precision, cuda
     else k_trap_fp64<2><<<L.trap_blocks, 128, 0, s>>>(D);
   }
 }
+
+// ---------------------------------------------------------------------------------------------
+// The field rectangle (Sec. 2: field particles interact only with massive bodies).  The
+// trapezoid's tiles cover the column blocks that hold massive bodies; every block of field
+// particles beyond them is one row of the rectangle N_m x N_field, taken by one warp: lane l
+// owns field particle b*32 + l, the system's massive bodies stream through a per-warp
+// shared-memory chunk of 32 (one coalesced load, then broadcast reads), and only the field
+// particle's side is accumulated -- a massless body exerts no force, so the massive side and the
+// per-tile partials of the trapezoid are not needed.  The sum over i runs in ascending order,
+// so the result does not depend on the launch or on other systems, and the kick
+// v += (tau/2) a is applied at the end (the reduction skips these blocks).  Kick 1 runs the same
+// fused encounter check as the tiles (FP32 prefilter, exact FP64 predicate, pair emission,
+// g_0 weight); kick 2 weights the flagged pairs through the groups.
+// ---------------------------------------------------------------------------------------------
+struct FieldSrc {
+  double x, y, z, gm;
+  float xf, yf, zf, xl, yl, zl, gmf;           // FP32 copies; low parts and G m (mixed)
+  float vxf, vyf, vzf, lam, sig;               // kick 1 prefilter
+  int id, ok, gid;
+};
+
+// stage massive bodies [c0, c0 + 32) of the system into the warp's chunk
+template <int MODE, bool MIXED>
+__device__ __forceinline__ void stage_sources(const Dev &D, const TileCtx &c, int c0, int lane, FieldSrc *src) {
+  const int li = c0 + lane;
+  FieldSrc s;
+  const int p = c.off + li;
+  s.id = p;
+  s.ok = (li < c.nm && D.alive[p]) ? 1 : 0;
+  const int q = s.ok ? p : c.off;               // a valid address for the loads below
+  s.x = D.x[q]; s.y = D.y[q]; s.z = D.z[q]; s.gm = D.gm[q];
+  s.xf = D.xf[q]; s.yf = D.yf[q]; s.zf = D.zf[q];
+  s.xl = 0.f; s.yl = 0.f; s.zl = 0.f; s.gmf = 0.f;
+  if (MIXED) {
+    s.xl = D.xl[q]; s.yl = D.yl[q]; s.zl = D.zl[q]; s.gmf = D.gmf[q];
+  }
+  s.vxf = 0.f; s.vyf = 0.f; s.vzf = 0.f; s.lam = 0.f; s.sig = 0.f;
+  if (MODE == 1) {
+    s.vxf = D.vxf[q]; s.vyf = D.vyf[q]; s.vzf = D.vzf[q]; s.lam = D.lamf[q]; s.sig = D.sigf[q];
+  }
+  s.gid = MODE == 2 ? D.gid[q] : -1;
+  src[lane] = s;
+}
+
+// the FP64 predicate of pair (i massive, p field) and, when flagged, its pair-list entry and
+// level-0 weight (1 when not flagged)
+__device__ __forceinline__ double field_check(const Dev &D, const TileCtx &c, int sys, int i, int p) {
+  const double ex = __dsub_rn(D.x[p], D.x[i]), ey = __dsub_rn(D.y[p], D.y[i]), ez = __dsub_rn(D.z[p], D.z[i]);
+  const double evx = __dsub_rn(D.vx[p], D.vx[i]), evy = __dsub_rn(D.vy[p], D.vy[i]),
+               evz = __dsub_rn(D.vz[p], D.vz[i]);
+  const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[i], D.rh[p]));
+  if (!encounter_exact(ex, ey, ez, evx, evy, evz, R0, c.dt)) return 1.0;
+  const int k = atomicAdd(&D.stat[sys].npairs, 1);
+  if (k < c.pair_cap) {
+    D.raw_i[c.pair_base + k] = i;
+    D.raw_j[c.pair_base + k] = p;
+  }
+  const double er2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return g0_weight(c, R0, __dsqrt_rn(er2));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_field_fp64(Dev D) {
+  __shared__ FieldSrc chunk[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 4 + w;
+  if (e >= D.nfblk) return;
+  const int2 fb = D.fblk[e];                     // {system, global block}
+  const TileCtx c = load_ctx(&D.disks[fb.x]);
+  FieldSrc *src = chunk[w];
+  const int p = fb.y * 32 + lane;
+  const int lp = p - c.off;
+  const bool live = lp < c.n && D.alive[p];
+  const double xp = D.x[p], yp = D.y[p], zp = D.z[p];
+  const float xfp = D.xf[p], yfp = D.yf[p], zfp = D.zf[p];
+  float vxfp = 0.f, vyfp = 0.f, vzfp = 0.f, lamp = 0.f, sigp = 0.f;
+  int gidp = -1;
+  if (MODE == 1) {
+    vxfp = D.vxf[p]; vyfp = D.vyf[p]; vzfp = D.vzf[p]; lamp = D.lamf[p]; sigp = D.sigf[p];
+  } else {
+    gidp = D.gid[p];
+  }
+  const float tauf = __double2float_ru(c.dt);
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int c0 = 0; c0 < c.nm; c0 += 32) {
+    __syncwarp();
+    stage_sources<MODE, false>(D, c, c0, lane, src);
+    __syncwarp();
+    const int cnt = min(32, c.nm - c0);
+#pragma unroll 1
+    for (int s = 0; s < cnt; ++s) {
+      const FieldSrc &q = src[s];
+      const bool valid = live && q.ok;
+      const double dx = q.x - xp, dy = q.y - yp, dz = q.z - zp;
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      double sp = q.gm * rinv3(r2);
+      if (MODE == 1) {
+        const float dxf = q.xf - xfp, dyf = q.yf - yfp, dzf = q.zf - zfp;
+        const float r2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
+        const float dvxf = q.vxf - vxfp, dvyf = q.vyf - vyfp, dvzf = q.vzf - vzfp;
+        const float vmag = sqrtf(fmaf(dvzf, dvzf, fmaf(dvyf, dvyf, dvxf * dvxf)));
+        const float Bf = fmaf(tauf, vmag, q.lam + lamp) * 1.0000039f + 1.9073486e-6f * (q.sig + sigp);
+        const bool cand = valid && !(r2f > Bf * Bf);
+        if (__any_sync(FULL, cand)) {
+          if (cand) sp *= field_check(D, c, fb.x, q.id, p);
+        }
+      } else if (gidp >= 0 && gidp == q.gid && valid) {
+        if (group_has_pair(D, gidp, q.id, p)) {
+          const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[q.id], D.rh[p]));
+          sp *= g0_weight(c, R0, sqrt(r2));
+        }
+      }
+      sp = keep_or_zero(sp, valid);
+      ax = fma(sp, dx, ax); ay = fma(sp, dy, ay); az = fma(sp, dz, az);
+    }
+  }
+  if (live) {
+    const double h = 0.5 * c.dt;
+    D.vx[p] = __dadd_rn(D.vx[p], __dmul_rn(h, ax));
+    D.vy[p] = __dadd_rn(D.vy[p], __dmul_rn(h, ay));
+    D.vz[p] = __dadd_rn(D.vz[p], __dmul_rn(h, az));
+  }
+}
+
+// Mixed precision: the same rectangle with the FP32 pair arithmetic of tile_mixed (two-float
+// displacement, FP32 rsqrt and one Newton step, Kahan-compensated FP32 sums carried into FP64
+// once); the encounter check is the FP64 one.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_field_mixed(Dev D) {
+  __shared__ FieldSrc chunk[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 4 + w;
+  if (e >= D.nfblk) return;
+  const int2 fb = D.fblk[e];
+  const TileCtx c = load_ctx(&D.disks[fb.x]);
+  FieldSrc *src = chunk[w];
+  const int p = fb.y * 32 + lane;
+  const int lp = p - c.off;
+  const bool live = lp < c.n && D.alive[p];
+  const float xhp = D.xf[p], yhp = D.yf[p], zhp = D.zf[p];
+  const float xlp = D.xl[p], ylp = D.yl[p], zlp = D.zl[p];
+  float vxfp = 0.f, vyfp = 0.f, vzfp = 0.f, lamp = 0.f, sigp = 0.f;
+  int gidp = -1;
+  if (MODE == 1) {
+    vxfp = D.vxf[p]; vyfp = D.vyf[p]; vzfp = D.vzf[p]; lamp = D.lamf[p]; sigp = D.sigf[p];
+  } else {
+    gidp = D.gid[p];
+  }
+  const float tauf = __double2float_ru(c.dt);
+  float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+  for (int c0 = 0; c0 < c.nm; c0 += 32) {
+    __syncwarp();
+    stage_sources<MODE, true>(D, c, c0, lane, src);
+    __syncwarp();
+    const int cnt = min(32, c.nm - c0);
+#pragma unroll 1
+    for (int s = 0; s < cnt; ++s) {
+      const FieldSrc &q = src[s];
+      const bool valid = live && q.ok;
+      const float dx = (q.xf - xhp) + (q.xl - xlp);
+      const float dy = (q.yf - yhp) + (q.yl - ylp);
+      const float dz = (q.zf - zhp) + (q.zl - zlp);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      float ri;
+      asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ri) : "f"(r2));
+      ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
+      float sp = q.gmf * (ri * ri * ri);
+      if (MODE == 1) {
+        const float dvxf = q.vxf - vxfp, dvyf = q.vyf - vyfp, dvzf = q.vzf - vzfp;
+        const float vmag = sqrtf(fmaf(dvzf, dvzf, fmaf(dvyf, dvyf, dvxf * dvxf)));
+        const float Bf = fmaf(tauf, vmag, q.lam + lamp) * 1.0000039f + 1.9073486e-6f * (q.sig + sigp);
+        const bool cand = valid && !(r2 > Bf * Bf * 1.0000153f);
+        if (__any_sync(FULL, cand)) {
+          if (cand) sp *= (float)field_check(D, c, fb.x, q.id, p);
+        }
+      } else if (gidp >= 0 && gidp == q.gid && valid) {
+        if (group_has_pair(D, gidp, q.id, p)) {
+          const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[q.id], D.rh[p]));
+          const double ex = D.x[p] - D.x[q.id], ey = D.y[p] - D.y[q.id], ez = D.z[p] - D.z[q.id];
+          sp *= (float)g0_weight(c, R0, sqrt(fma(ez, ez, fma(ey, ey, ex * ex))));
+        }
+      }
+      if (!valid) sp = 0.f;
+      kahan(sx, cx, sp * dx); kahan(sy, cy, sp * dy); kahan(sz, cz, sp * dz);
+    }
+  }
+  if (live) {
+    const double h = 0.5 * c.dt;
+    D.vx[p] = fma(h, (double)sx - (double)cx, D.vx[p]);
+    D.vy[p] = fma(h, (double)sy - (double)cy, D.vy[p]);
+    D.vz[p] = fma(h, (double)sz - (double)cz, D.vz[p]);
+  }
+}
+
+void launch_field(const Dev &D, int mode, int precision, cudaStream_t s) {
+  if (D.nfblk <= 0) return;
+  const int blocks = (D.nfblk + 3) / 4;
+  if (precision == SYMBA_PRECISION_MIXED) {
+    if (mode == 1) k_field_mixed<1><<<blocks, 128, 0, s>>>(D);
+    else k_field_mixed<2><<<blocks, 128, 0, s>>>(D);
+  } else {
+    if (mode == 1) k_field_fp64<1><<<blocks, 128, 0, s>>>(D);
+    else k_field_fp64<2><<<blocks, 128, 0, s>>>(D);
+  }
+}

@@ -1,7 +1,8 @@
 """Small, self-contained workloads for profiling single kernels (ncu, CUDA events).
 
-    python -m paper_2304_07325_gb300.profile_cases step --n 10000 [--precision mixed]
-        one step of the Sec. 3 disk; the trapezoid kicks (k_trap_*) run twice
+    python -m paper_2304_07325_gb300.profile_cases step --n 10000 [--precision mixed] [--n-field F]
+        one step of the Sec. 3 disk (plus F field particles); the trapezoid kicks (k_trap_*) and,
+        with field particles, the field rectangle (k_field_*) run twice
     python -m paper_2304_07325_gb300.profile_cases bound_pair [--steps 1]
         one step of a 5-body encounter group of the 10,000-body disk (seed 1002) that holds a
         bound pair: the group recursion (k_recursion) dominates, ~34,000 sub-steps per step
@@ -26,16 +27,18 @@ def main(argv=None):
     ap.add_argument("case", choices=["step", "bound_pair", "steps"])
     ap.add_argument("--n", type=int, default=10000)
     ap.add_argument("--seed", type=int, default=1002)
+    ap.add_argument("--n-field", type=int, default=0, help="step / steps: massless field particles")
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     a = ap.parse_args(argv)
     prec = SYMBA_PRECISION_MIXED if a.precision == "mixed" else SYMBA_PRECISION_FP64
-    d = disk.planetesimal_disk(a.n if a.case == "step" else 10000, a.seed)
+    d = disk.planetesimal_disk(10000 if a.case == "bound_pair" else a.n, a.seed,
+                               n_field=0 if a.case == "bound_pair" else a.n_field)
     if a.case == "bound_pair":
         g = BOUND_PAIR_GROUP
         s = System(d.x[g], d.v[g], d.m[g], d.radius[g], params=default_params(precision=prec))
     else:
-        s = System(d.x, d.v, d.m, d.radius, params=default_params(precision=prec))
+        s = System(d.x, d.v, d.m, d.radius, n_massive=d.n_massive, params=default_params(precision=prec))
     if a.case == "steps":
         print("step substeps pair_substeps general_substeps max_chain recursion_ms")
         status = 0

@@ -67,8 +67,10 @@ class ServeStats:
 
 
 def tiles_for(n: int, n_massive: int) -> int:
-    nb, nbm = (n + 31) // 32, (n_massive + 31) // 32
-    return sum(nb - i for i in range(nbm))
+    """Trapezoid tiles of a system: 32 x 32 blocks (I, J), I <= J, over the column blocks that
+    hold massive bodies (blocks of field particles only form the field rectangle instead)."""
+    nbm = (n_massive + 31) // 32
+    return nbm * (nbm + 1) // 2
 
 
 class Server:
