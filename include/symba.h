@@ -90,7 +90,10 @@ typedef struct symba_pool symba_pool;
  * lambda 6.5, G 4 pi^2, m0 1, max_depth 20, FP64.  Never fails. */
 void symba_default_params(symba_params *p);
 
-/* Creates a context for one system and uploads it.
+/* Creates a context for one system and uploads it (Sec. 2: N particles, the first N_m massive and
+ * the rest massless field particles that interact only with massive ones; Sec. 3: the method's
+ * parameters in *p).  The velocities are turned into the democratic-heliocentric state the
+ * SyMBA step keeps (barycentric v = v_hel - sum m v_hel / (m0 + sum m)).
  * n, n_massive: particle counts (0 <= n_massive <= n, n >= 1).
  * x, v: n x 3 heliocentric positions and velocities; m, radius: n masses (0 for field particles)
  * and physical radii (contact detection); rhill: n Hill radii, or NULL to compute them as
@@ -101,7 +104,9 @@ int symba_init(symba_ctx **out, const symba_params *p, int n, int n_massive, con
                const double *v, const double *m, const double *radius, const double *rhill,
                void *cuda_stream);
 
-/* Enqueues nsteps SyMBA steps E(tau) on the context's stream and returns without waiting.
+/* Enqueues nsteps SyMBA steps E(tau) on the context's stream and returns without waiting
+ * (Sec. 2: the trapezoid kick, the encounter check with grouping, the groups integrated
+ * separately, the simple per-particle loops; Sec. 3: M, R_k/R_{k+1}, l).
  * Each step: sun drift tau/2; level-0 check fused into kick tau/2 over the trapezoid; grouping;
  * Kepler drift tau of bodies in no encounter and M-fold recursion of every group; kick tau/2;
  * removal by rmin / rmax (when set); sun drift tau/2.  Returns SYMBA_OK, SYMBA_E_INVAL (nsteps < 0) or SYMBA_E_CUDA. */
@@ -127,13 +132,16 @@ int symba_step_many(symba_ctx *const *ctxs, int n, int nsteps);
 int symba_energy(symba_ctx *c, double *E, double L[3]);
 
 /* The level-0 encounter pairs of the last step in ascending (i, j) order (i < j) and, for each,
- * the index of its group; groups are numbered by ascending smallest member.  pairs: 2 x cap
+ * the index of its group; groups are numbered by ascending smallest member (Sec. 2, encounter
+ * paragraph: pairs found by the check join groups that are integrated independently).  pairs: 2 x cap
  * ints, group_of_pair: cap ints (host or device).  *n_pairs and *n_groups receive the full
  * counts even when they exceed cap (then only cap entries are written).  Synchronises. */
 int symba_enc_groups(symba_ctx *c, int *pairs, int *group_of_pair, int cap, int *n_pairs,
                      int *n_groups);
 
-/* Copies the state out: x (n x 3 heliocentric), v (n x 3 barycentric), and optionally m,
+/* Copies the integrator's state out (the democratic-heliocentric split of SyMBA, which the paper
+ * parallelises without changing; Sec. 2): x (n x 3 heliocentric), v (n x 3 barycentric; the
+ * heliocentric velocity is v + P / m0 with P = sum m v), and optionally m,
  * radius (n) and alive (n ints, 0 for a body merged into another or removed).  Any output may be NULL.
  * Synchronises. */
 int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radius, int *alive);
@@ -146,14 +154,16 @@ int symba_get_state(symba_ctx *c, double *x, double *v, double *m, double *radiu
  * paragraph; Sec. 3 for the shell ratio).  Synchronises; returns the sticky status. */
 int symba_get_rhill(symba_ctx *c, double *rhill);
 
-/* Replaces positions (heliocentric) and barycentric velocities; masses, radii and Hill radii
+/* Replaces positions (heliocentric) and barycentric velocities -- the state symba_get_state
+ * returns, so a get/set round trip is exact (checkpoint and resume); masses, radii and Hill radii
  * stay.  Enqueued on the context's stream.  Also clears the sticky status. */
 int symba_set_state(symba_ctx *c, const double *x, const double *v);
 
-/* Diagnostics of the last call; synchronises. */
+/* Diagnostics of the last call (encounter pairs and groups, Sec. 2; recursion depth and sub-steps,
+ * Sec. 3); synchronises. */
 int symba_get_stats(symba_ctx *c, symba_stats *s);
 
-/* Phase timing (tracing): runs nsteps steps like symba_step, launching the kernels one by one
+/* Phase timing (tracing; the paper times whole runs, Sec. 3): runs nsteps steps like symba_step, launching the kernels one by one
  * with CUDA events between them on the context's stream, then synchronises and writes the
  * summed device time of each phase in milliseconds to phase_ms[0..SYMBA_NPHASES-1] (host):
  * 0 sun drift + step prologue, 1 kick 1 with the fused encounter check, 2 kick-1 reduction,
@@ -192,7 +202,10 @@ int symba_pool_step(symba_pool *pool, int nsteps);
 /* Waits; returns the worst sticky status over the pool's systems. */
 int symba_pool_sync(symba_pool *pool);
 
-/* Per-system state, energy and diagnostics (synchronising; arguments as the symba_* forms). */
+/* Per-system state, energy, Hill radii, encounter list and diagnostics (synchronising) and
+ * set-state (enqueued), with the arguments, meaning and errors of the single-system forms
+ * symba_get_state, symba_energy, symba_get_rhill, symba_enc_groups, symba_set_state and
+ * symba_get_stats; slot is the id symba_pool_admit returned (SYMBA_E_INVAL otherwise). */
 int symba_pool_get_state(symba_pool *pool, int slot, double *x, double *v, double *m,
                          double *radius, int *alive);
 int symba_pool_energy(symba_pool *pool, int slot, double *E, double L[3]);

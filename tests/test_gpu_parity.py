@@ -123,7 +123,14 @@ def test_100_steps_positions_1e12(orc, sy):
     x, v, m, r, a = gpu.get_state()
     assert np.array_equal(a, ref.alive)
     rel, spread = _check_positions(x, ref, twin)
-    assert np.mean(rel <= 1e-12) > 0.9
+    # printed so that a regression shows before it fails: the share of bodies at 1e-12, and how
+    # far the others are from the twin's spread
+    frac = float(np.mean(rel <= 1e-12))
+    over = rel > 1e-12
+    worst = float(np.max(rel[over] / np.maximum(spread[over], 1e-300))) if over.any() else 0.0
+    print(f"100 steps, N = 1,000: {100 * frac:.1f} % of bodies within 1e-12; the other {int(over.sum())} "
+          f"within {worst:.2f}x the twin's spread (bound 100x); median {np.median(rel):.2e}, max {rel.max():.2e}")
+    assert frac > 0.9
     E_ref, _ = ref.energy()
     E_gpu, _ = gpu.energy()
     assert abs(E_gpu - E_ref) <= 1e-12 * abs(E_ref)
