@@ -338,6 +338,19 @@ __device__ __forceinline__ void sa_add(unsigned long long *dig, double x) {
   if (c2) atomicAdd(&dig[k + 2], (unsigned long long)c2);
 }
 
+// Carry propagation in place (one thread): the same value with digits 0..SA_NDIG-2 in [0, 2^32)
+// and the sign in the top digit.  A CTA that has summed many terms into its own digits adds them
+// to a shared accumulator in this form, so each atomic brings less than 2^32 per digit and the
+// shared digits stay far from overflow however many CTAs contribute.
+__device__ inline void sa_carry(unsigned long long *dig) {
+  for (int k = 0; k < SA_NDIG - 1; ++k) {
+    const long long v = (long long)dig[k];
+    const long long c = v >> 32;
+    dig[k] = (unsigned long long)(v - c * 4294967296ll);
+    dig[k + 1] = (unsigned long long)((long long)dig[k + 1] + c);
+  }
+}
+
 __device__ inline double sa_round(const unsigned long long *in) {
   if (in[SA_NDIG] != 0ull) return __longlong_as_double(0x7FF8000000000000ll);
   long long d[SA_NDIG];

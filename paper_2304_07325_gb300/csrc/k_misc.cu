@@ -490,6 +490,9 @@ __global__ void __launch_bounds__(256) k_energy_pairs(Dev D, int d, unsigned lon
     }
   }
   __syncthreads();
+  // O(N^2) terms over all CTAs: hand the shared accumulator this CTA's digits carried
+  if (threadIdx.x == 0) sa_carry(sacc);
+  __syncthreads();
   for (int k = threadIdx.x; k < SA_NDIG + 1; k += blockDim.x) {
     const unsigned long long v = sacc[k];
     if (v) atomicAdd(&acc[k], v);
