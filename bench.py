@@ -78,6 +78,9 @@ def parse():
                     help="single mode: skip the 64-disk batched comparison at matched accuracy")
     ap.add_argument("--no-served", action="store_true",
                     help="single mode: skip the served Poisson stream at matched accuracy")
+    ap.add_argument("--no-field", action="store_true",
+                    help="single mode: skip the field-dominated disk (1,000 + 100,000) against the oracle")
+    ap.add_argument("--field-steps", type=int, default=3)
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--served-requests", type=int, default=16)
     ap.add_argument("--served-steps-cap", type=int, default=10)
@@ -474,7 +477,49 @@ def chain_vs_cpu(sy, disk):
             "oracle_host": host_cpu()["model"]}
 
 
+def bench_field_small(sy, disk, steps, oracle_res):
+    """Config-3 shape in the default line: N_m = 1,000 + 100,000 field particles (seed 1003),
+    `steps` steps of the mixed and the FP64 path (the field rectangle does the kicks), each against
+    the FP64 oracle's state after the same steps (computed meanwhile on the host)."""
+    d = disk.planetesimal_disk(1000, 1003, n_field=100000)
+    P = 1000 * 999 // 2 + 1000 * 100000
+    out = {"workload": "field-dominated disk N_m=1000 + 100000 massless (seed 1003), dt=0.5 yr, M=4, "
+                       "R_k/R_k+1=2.08, l=3", "steps": steps, "pairs_per_kick": P}
+    for name, prec in (("mixed", sy.SYMBA_PRECISION_MIXED), ("fp64", sy.SYMBA_PRECISION_FP64)):
+        s = sy.System(d.x, d.v, d.m, d.radius, n_massive=1000, params=sy.default_params(precision=prec))
+        E0, _ = s.energy()
+        ph = s.profile_step(steps)
+        if s.sync() < 0:
+            raise RuntimeError(f"field {name}: {sy.status_string(s.sync())}")
+        x, *_ = s.get_state()
+        E1, _ = s.energy()
+        s.close()
+        kick_ms = float(ph[1] + ph[6]) / (2 * steps)
+        r = {"ms_per_step": float(ph.sum()) / steps, "kick_ms": kick_ms,
+             "pairs_per_s": 2.0 * P * steps / (float(ph.sum()) * 1e-3), "dE_rel": abs((E1 - E0) / E0)}
+        if oracle_res is not None and oracle_res.get("status", -1) >= 0:
+            rel = np.linalg.norm(x - oracle_res["x"], axis=1) / np.linalg.norm(oracle_res["x"], axis=1)
+            r["vs_oracle"] = {"position_p50": float(np.median(rel)), "position_p99": float(np.percentile(rel, 99)),
+                              "position_max": float(rel.max()),
+                              "dE_minus_oracle": abs((E1 - oracle_res["E1"]) / E0)}
+        out[name] = r
+    if oracle_res is not None:
+        out["oracle_seconds"] = oracle_res.get("seconds")
+    return out
+
+
 def run_ours(args):
+    # the oracle's run of the field-dominated disk, on a host core while the GPU works (spawned
+    # before the first CUDA call)
+    oracle_field = None
+    rank0, world0, _ = dist_env()
+    if rank0 == 0 and world0 == 1 and not args.no_field and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        conn, child_conn = ctx.Pipe(duplex=False)
+        proc = ctx.Process(target=_oracle_field_run, args=(1000, 100000, 1003, args.field_steps, child_conn))
+        proc.start()
+        oracle_field = (proc, conn)
     import torch
     import torch.distributed as dist
 
@@ -629,6 +674,13 @@ def run_ours(args):
         batched = None if args.no_batched or world > 1 else bench_batched(sy, disk, args.batched_steps, 1, 2)
         served = None if args.no_served or world > 1 else bench_served(sy, args.served_requests,
                                                                           args.served_steps_cap)
+        field = None
+        if not args.no_field and world == 1:
+            ores = None
+            if oracle_field is not None:
+                ores = oracle_field[1].recv()
+                oracle_field[0].join()
+            field = bench_field_small(sy, disk, args.field_steps, ores)
         line = {"metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -653,7 +705,7 @@ def run_ours(args):
                 # loop times each step as its own call; the launch list shows the same 13)
                 "gpu_launches": args.steps * 13,
                 "clocks": clk, "wall_s": wall, "second": second, "rates": rates,
-                "chain_vs_cpu": chain, "batched": batched, "served": served}
+                "chain_vs_cpu": chain, "batched": batched, "served": served, "field": field}
         print(json.dumps(line), flush=True)
     sysm.close()
     if world > 1:
