@@ -16,7 +16,7 @@
 
 #define SYM_TILE 32
 #define SYM_MAX_LEVELS 32
-#define SYM_PAIR_LC (17 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
+#define SYM_PAIR_LC (16 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
 #define SYM_REC_BPSM_MAX 2   // recursion CTAs per SM a schedule may ask for
 #define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
 

@@ -517,11 +517,20 @@ __device__ __forceinline__ double rsq_est(double r2, float r2e) {
 // Branch-free forms for the straight common sub-step (a branch would end the block the
 // scheduler interleaves): ok reports whether the seed was in range; the caller votes on it and
 // takes the forms above when any lane was not.
+//
+// The correction y0 + e (y0/2 + e 3y0/8) takes three FP64 instructions: y0/2 and 3y0/8 are exact
+// (a 24-bit significand times 3 fits) and built from the seed's bits on the integer pipe, before
+// r2 -- which the FP64 instructions wait for -- is ready.
 __device__ __forceinline__ double rsq_nb(double r2, float r2e, bool &ok) {
   double y0, t;
-  seed_nb(r2e, y0, t, ok);
+  float y0f;
+  seed_nb(r2e, y0, t, ok, y0f);
+  const unsigned b = __float_as_uint(y0f);
+  const double y0h = __longlong_as_double(__double_as_longlong(y0) - (1ll << 52));      // y0 / 2
+  const double y038 = u64_scaled(3ull * ((b & 0x7FFFFFu) | 0x800000u),               // 3 y0 / 8
+                                 (int)((b >> 23) & 0xFFu) - 153);
   const double e = fma(-r2, t, 1.0);
-  return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+  return fma(e, fma(e, y038, y0h), y0);
 }
 // r2^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8) to e^3 ~ 2^-62, with y0^3 = t y0;
 // also t and e, from which 1/r2 = t (1 + e + e^2).  Every lane of the warp must call it.
@@ -542,7 +551,7 @@ __device__ __forceinline__ double rinv3_est(double r2, float r2e, double &t, dou
 // per-level constants of the single-pair path, cached in shared memory
 enum {
   LC_H, LC_HH, LC_T2, LC_R2, LC_A1, LC_B1, LC_A2, LC_B2, LC_GHA, LC_GHB, LC_T3, LC_MUNH, LC_H15,
-  LC_MUNH15, LC_R2N, LC_R2P, LC_MUNH1875, LC_N
+  LC_MUNH15, LC_R2N, LC_R2P, LC_N
 };
 
 // Runs the sub-steps of levels >= k with F_{k-1} = {q}, from the opening of a sub-step at level
@@ -588,7 +597,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // current level's constants
   // (h^2, h^3 and 1.5 h serve only the order-3 drift, which reads them from the cache)
-  double h, hh, R2, A1, B1, A2, B2, ghs, munh, munh15, munh1875, R2n, R2p;
+  double h, hh, R2, A1, B1, A2, B2, ghs, munh, munh15, R2n, R2p;
   float hf, R2f;
   auto set_level = [&](int jj) {
     double *Lc = lc + LC_N * jj;
@@ -609,8 +618,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       const double v[LC_N] = {hj, hh_, t2_, cpy(s1, lane, 2), cpy(s2, lane, 0), -cpy(s2, lane, 1),
                               cpy(s2, lane, 2), -cpy(s2, lane, 3), cpy(s3, lane, 0),
                               cpy(s3, lane, 1), cpy(s3, lane, 2), cpy(s3, lane, 3), cpy(s4, lane, 1),
-                              cpy(s3, lane, 3) * 1.5, cpy(s1, lane, 3), cpy(s4, lane, 2),
-                              cpy(s3, lane, 3) * 1.875};
+                              cpy(s3, lane, 3) * 1.5, cpy(s1, lane, 3), cpy(s4, lane, 2)};
 #pragma unroll
       for (int i = 0; i < LC_N; ++i) Lc[i] = v[i];
       have |= 1ull << jj;
@@ -619,7 +627,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
     ghs = flip(Lc[pb ? LC_GHA : LC_GHB], sgn_b);       // -G m_a h/2 on body b, G m_b h/2 on a
     munh = Lc[LC_MUNH];
-    munh15 = Lc[LC_MUNH15]; munh1875 = Lc[LC_MUNH1875];
+    munh15 = Lc[LC_MUNH15];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
     hf = f32_trunc(h);
     R2f = f32_trunc(R2) * (1.0f + 3.0517578e-5f);     // not below R2
@@ -907,8 +915,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         body_r_nb();
         const bool far = far_apart(U);
         unsigned ord = drift_order_nb();
-        // the order-2 drift as in drift(2), with f' = -mu h/r^3 straight from the seed terms
-        const double fd = rbty * fma(rbe, fma(rbe, munh1875, munh15), munh);
+        // the order-2 drift as in drift(2), with f' = -mu h/r^3 straight from the seed terms,
+        // y0^3 (1 + 3e/2) (-mu h): the series' next term, 15/8 e^2 < 2^-42, is dropped -- in the
+        // order-2 regime f' x is below 1e-6 of v (h n < 1e-6), so it moves v by < 2^-62 of v
+        const double fd = rbty * fma(rbe, munh15, munh);
         const double W = fma(fd, X, V), Y = fma(hh, V, X);
         const double Xn = fma(hh, W, Y);
         const double Vn = fma(fd, Y, V);
