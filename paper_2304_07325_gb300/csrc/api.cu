@@ -18,7 +18,7 @@ namespace {
 
 struct Slot {
   bool active = false;
-  int off = 0, n = 0, nm = 0, nb = 0, nbm = 0, ntiles = 0, pair_base = 0, pair_cap = 0;
+  int off = 0, n = 0, nm = 0, nb = 0, nbm = 0, ntiles = 0, nmacro = 0, pair_base = 0, pair_cap = 0;
   symba_params p{};
   long long merges_reported = 0;
 };
@@ -53,6 +53,23 @@ struct RangeAlloc {
 // (blocks of field particles only are rows of the field rectangle instead)
 long long tiles_of(int nbm) { return (long long)nbm * (nbm + 1) / 2; }
 
+// macro-tiles (row quads q of 4 blocks by column groups g of SYM_MACRO_COLS blocks, g from
+// 4q / SYM_MACRO_COLS) of a system with nbm massive blocks
+long long macros_of(int nbm) {
+  const long long C = SYM_MACRO_COLS, nq = (nbm + 3) / 4, ng = (nbm + C - 1) / C;
+  long long m = 0;
+  for (long long q = 0; q < nq; ++q) m += ng - (4 / C) * q;
+  return m;
+}
+
+// Macro-tiles a pool sized for max_tiles tiles over up to max_disks systems can need: a system of
+// T tiles has nbm <= sqrt(2T) blocks and at most T / (4 C) + sqrt(2T) + 2 macro-tiles (checked
+// for every nbm up to 20,000 in tests/test_abi.py), and each system's T is at most max_tiles.
+long long macro_capacity(long long max_tiles, int max_disks) {
+  const double root = std::sqrt(2.0 * (double)max_tiles);
+  return max_tiles / (4 * SYM_MACRO_COLS) + (long long)max_disks * ((long long)std::ceil(root) + 2);
+}
+
 int default_pair_cap(const symba_params *p, int n) {
   if (p && p->pair_capacity > 0) return p->pair_capacity;
   return std::max(4096, 4 * n);
@@ -71,6 +88,7 @@ struct symba_pool {
   std::vector<Slot> slots;
   RangeAlloc parts, pairs;
   long long tiles_used = 0;
+  long long mcap = 0, macros_used = 0;       // macro-tiles: capacity and in use
   long long npart_hwm = 0;
   int ndisks = 0;
   std::vector<void *> allocs;
@@ -165,7 +183,7 @@ int rebuild(symba_pool *P) {
     if (!s.active) continue;
     dd.off = s.off; dd.n = s.n; dd.nm = s.nm; dd.nb = s.nb; dd.nbm = s.nbm;
     dd.tile_base = (int)tiles.size();
-    dd.ntiles = s.ntiles;
+    dd.ntiles = s.nmacro;
     dd.pair_base = s.pair_base; dd.pair_cap = s.pair_cap;
     dd.group_base = s.off / 2;
     dd.active = 1;
@@ -177,8 +195,9 @@ int rebuild(symba_pool *P) {
     dd.rmax2 = s.p.rmax > 0.0 ? s.p.rmax * s.p.rmax : 0.0;
     any_discard = any_discard || dd.rmin2 > 0.0 || dd.rmax2 > 0.0;
     const int b0 = s.off / SYM_TILE;
-    for (int I = 0; I < s.nbm; ++I)
-      for (int J = I; J < s.nbm; ++J) tiles.push_back(make_int4(d, b0 + I, b0 + J, 0));
+    const int C = SYM_MACRO_COLS, nq = (s.nbm + 3) / 4, ng = (s.nbm + C - 1) / C;
+    for (int q = 0; q < nq; ++q)
+      for (int g = (4 / C) * q; g < ng; ++g) tiles.push_back(make_int4(d, b0 + 4 * q, b0 + C * g, b0 + s.nbm));
     for (int B = s.nbm; B < s.nb; ++B) fblk.push_back(make_int2(d, b0 + B));
   }
   P->ndisks = hw;
@@ -186,9 +205,9 @@ int rebuild(symba_pool *P) {
   P->any_discard = any_discard;
   P->D.ndisks = hw;
   P->D.ntiles_total = (int)tiles.size();
-  const long long warps = (long long)P->L.trap_blocks * 4;
-  long long seg = (long long)tiles.size() / std::max(1LL, warps * 24);
-  P->D.seg_len = P->seg_override > 0 ? P->seg_override : (int)std::max(1LL, std::min(8LL, seg));
+  // macro-tiles per grab: one unless there are many per CTA
+  long long seg = (long long)tiles.size() / std::max(1LL, (long long)P->L.trap_blocks * 8);
+  P->D.seg_len = P->seg_override > 0 ? P->seg_override : (int)std::max(1LL, std::min(4LL, seg));
   if (!tiles.empty())
     CK(cudaMemcpyAsync(P->D.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, P->stream));
   P->D.nfblk = (int)fblk.size();
@@ -335,6 +354,7 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   P->precision = precision;
   P->pcap = ((max_particles + SYM_TILE - 1) / SYM_TILE) * SYM_TILE + (long long)SYM_TILE * max_disks;
   P->tcap = max_tiles;
+  P->mcap = macro_capacity(max_tiles, max_disks);
   P->paircap = pair_total;
   if (stream) P->stream = (cudaStream_t)stream;
   else {
@@ -363,9 +383,9 @@ int pool_create(symba_pool **out, int max_disks, long long max_particles, long l
   A(&D.blk_disk, n / SYM_TILE + 1);
   A(&D.disks, max_disks); A(&D.stat, max_disks); A(&D.P, 3 * max_disks);
   A(&D.sacc, (size_t)max_disks * 3 * (SA_NDIG + 1));
-  A(&D.tiles, P->tcap);
+  A(&D.tiles, P->mcap);
   A(&D.fblk, n / SYM_TILE + 1);
-  A(&D.part, (size_t)P->tcap * 2 * 3 * 32);
+  A(&D.part, (size_t)P->mcap * SYM_MACRO_PART);
   A(&D.work, 4);
   A(&D.raw_i, pc); A(&D.raw_j, pc); A(&D.pi, pc); A(&D.pj, pc); A(&D.gop, pc);
   A(&D.gpi, pc); A(&D.gpj, pc); A(&D.lev, pc); A(&D.tmpj, pc);
@@ -416,8 +436,9 @@ int pool_admit(symba_pool *P, const symba_params *p, int n, int nm, const double
   s.nb = (n + SYM_TILE - 1) / SYM_TILE;
   s.nbm = (nm + SYM_TILE - 1) / SYM_TILE;
   s.ntiles = (int)tiles_of(s.nbm);
+  s.nmacro = (int)macros_of(s.nbm);
   s.pair_cap = default_pair_cap(p, n);
-  if (P->tiles_used + s.ntiles > P->tcap) return SYMBA_E_NOMEM;
+  if (P->tiles_used + s.ntiles > P->tcap || P->macros_used + s.nmacro > P->mcap) return SYMBA_E_NOMEM;
   const long long po = P->parts.alloc((long long)s.nb * SYM_TILE);
   if (po < 0) return SYMBA_E_NOMEM;
   const long long pb = P->pairs.alloc(s.pair_cap);
@@ -427,6 +448,7 @@ int pool_admit(symba_pool *P, const symba_params *p, int n, int nm, const double
   s.active = true;
   P->slots[d] = s;
   P->tiles_used += s.ntiles;
+  P->macros_used += s.nmacro;
   // block -> system map
   std::vector<int> bd(s.nb, d);
   CK(cudaMemcpyAsync(P->D.blk_disk + s.off / SYM_TILE, bd.data(), sizeof(int) * s.nb, cudaMemcpyHostToDevice, P->stream));
@@ -832,7 +854,7 @@ long long symba_pool_footprint(int n, int n_massive, const symba_params *p) {
   const long long per_particle = 20 * 8 + 3 * 4 + 12 * 4 + 12 * 4 + 3 * 8 + 6 * 4 / 2 + 4;
   const long long pairs = default_pair_cap(p, n);
   const long long per_pair = 13 * 4 + 7 * 8 + 2 * 4;
-  return np * per_particle + pairs * per_pair + tiles_of((int)nbm) * (16 + 2 * 3 * 32 * 8) + 8 * nb;
+  return np * per_particle + pairs * per_pair + macros_of((int)nbm) * (16 + SYM_MACRO_PART * 8) + 8 * nb;
 }
 
 int symba_pool_create(symba_pool **out, int max_systems, long long max_particles, long long max_tiles,
@@ -908,6 +930,7 @@ int symba_pool_evict(symba_pool *pool, int slot) {
   pool->parts.release(s.off, (long long)s.nb * SYM_TILE);
   pool->pairs.release(s.pair_base, s.pair_cap);
   pool->tiles_used -= s.ntiles;
+  pool->macros_used -= s.nmacro;
   s = Slot();
   return rebuild(pool);
 }

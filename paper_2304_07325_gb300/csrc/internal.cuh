@@ -5,9 +5,12 @@
 //   x, y, z, vx, vy, vz, m, gm (= G m), rad, rh   : FP64 SoA, heliocentric x, barycentric v
 //   alive, gid                                     : int per particle (gid = encounter group or -1)
 //   xf, yf, zf, vxf, vyf, vzf, lamf, sigf          : FP32 copies for the encounter prefilter
-//   tiles                                          : int4 {system, I-block, J-block, 0} per 32x32 tile
+//   tiles                                          : int4 {system, first row block, first column block,
+//                                                    end of the massive blocks} per 4 x 4 macro-tile
+//                                                    of 32 x 32 tiles (128-body quads q <= c)
 //   fblk                                           : int2 {system, block} per block of field particles
-//   part                                           : FP64 [tile][2 sides][3][32] pair-kick partials
+//   part                                           : FP64 [macro-tile][rows, columns][4][3][32]
+//                                                    pair-kick partials
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,10 +22,15 @@
 #define SYM_PAIR_LC (16 * (SYM_MAX_LEVELS + 2))   // level-constant cache of one recursion warp
 #define SYM_REC_BPSM_MAX 2   // recursion CTAs per SM a schedule may ask for
 #define SA_NDIG 68  // 32-bit digits of the exact accumulator, digit k weighs 2^(32k - 1088)
+#ifndef SYM_MACRO_COLS
+#define SYM_MACRO_COLS 2     // column blocks of a macro-tile (its rows: 4 blocks, one per warp)
+#endif
+#define SYM_MACRO_PART ((4 + SYM_MACRO_COLS) * 96)   // partials of a macro-tile: rows, then columns,
+                                                     // [block][3][32] each
 
 struct DiskDesc {
   int off, n, nm, nb, nbm;      // first particle, counts, 32-blocks (all, massive rows)
-  int tile_base, ntiles;        // this system's tiles in the global tile list
+  int tile_base, ntiles;        // this system's macro-tiles in the global list
   int pair_base, pair_cap;      // this system's slice of the pair buffers
   int group_base;               // this system's slice of the group slots (= off / 2)
   int active, M, l, max_depth, max_substeps, pad0;
@@ -55,13 +63,13 @@ struct Dev {
   double *P;                    // [max_disks][3] total barycentric momentum (for the sun drift)
   unsigned long long *sacc;     // [max_disks][3][SA_NDIG + 1] exact accumulators
   // trapezoid
-  int4 *tiles;                  // tiles (I, J), I <= J < ceil(N_m / 32): column blocks holding massive bodies
-  double *part;                 // [tile][2][3][32]
+  int4 *tiles;                  // macro-tiles (quads q <= c) over the blocks holding massive bodies
+  double *part;                 // [macro-tile][SYM_MACRO_PART]
   int2 *fblk;                   // field rectangle: {system, block} of every block of field particles only
   int nfblk;
   int *work;                    // [4] dynamic work counters (kick 1, kick 2, recursion, spare)
   int ntiles_total;
-  int seg_len;                  // tiles per work item
+  int seg_len;                  // macro-tiles per work item
   int ndisks;                   // slots in use (upper bound of active slots)
   // encounter pairs (pair-indexed, per-system slices)
   int *raw_i, *raw_j;           // appended by the fused check, unordered

@@ -245,11 +245,14 @@ void launch_sundrift(const Dev &D, long long npart, int pre, cudaStream_t s) {
 
 // --------------------------------------------------------------------------------------------
 // kick: a_p = fixed-order sum of the trapezoid partials that touch p, then v_p = v_p + (tau/2) a_p.
-// Row partials (side 0) of tiles (B, J), J = B..nb-1, then column partials (side 1) of tiles
-// (I, B), I = 0..min(B, nbm)-1; the diagonal tile's column side is folded into its row side.
+// Macro-tiles are (row quad q, column group g), C = SYM_MACRO_COLS column blocks per group, g from
+// 4q / C; block B of the system has its row partials in (B/4, g), g = 4(B/4)/C..ng-1 (row slot
+// B % 4), then its column partials in (q, B/C), q = 0..B/4 (column slot B % C; the diagonal
+// tiles' column sides are folded into their rows).  Macro-tile (q, g) is entry
+// tile_base + q ng - (4/C) q (q - 1)/2 + (g - 4q/C) of the list.
 // --------------------------------------------------------------------------------------------
-__device__ __forceinline__ int row_start(const DiskDesc &dd, int I) {
-  return dd.tile_base + I * dd.nbm - (I * (I - 1)) / 2;
+__device__ __forceinline__ int macro_index(const DiskDesc &dd, int ng, int q, int g) {
+  return dd.tile_base + q * ng - (4 / SYM_MACRO_COLS) * ((q * (q - 1)) / 2) + (g - (4 / SYM_MACRO_COLS) * q);
 }
 
 __global__ void k_reduce(Dev D, long long npart) {
@@ -263,26 +266,26 @@ __global__ void k_reduce(Dev D, long long npart) {
     if (li >= dd.n || !D.alive[p]) continue;
     const int B = li >> 5, lane = li & 31;
     if (B >= dd.nbm) continue;                  // a block of field particles: kicked by k_field_*
-    // the partials of p in a fixed order (its row, then its column), as a list of tile slots;
-    // two interleaved sums (even and odd terms) keep two loads in flight, combined at the end
-    const int nrow = dd.nbm - B;
-    const int Imax = B < dd.nbm ? B : dd.nbm;
-    const int nterm = nrow + Imax;
-    const int t0 = nrow ? row_start(dd, B) : 0;
-    auto slot = [&](int q) -> const double * {
-      if (q < nrow) return D.part + ((size_t)(t0 + q) * 2 * 3) * 32 + lane;
-      const int I = q - nrow;
-      return D.part + (((size_t)(row_start(dd, I) + (B - I)) * 2 + 1) * 3) * 32 + lane;
+    const int C = SYM_MACRO_COLS, ng = (dd.nbm + C - 1) / C, qB = B >> 2, gB = B / C;
+    const int rslot = (B & 3) * 96 + lane, cslot = 384 + (B % C) * 96 + lane;
+    // the partials of p in a fixed order (its rows, then its columns); two interleaved sums
+    // (even and odd terms) keep two loads in flight, combined at the end
+    const int g0 = (4 / C) * qB, nrow = ng - g0;
+    const int nterm = nrow + qB + 1;
+    auto ptr = [&](int t) -> const double * {
+      if (t < nrow) return D.part + (size_t)macro_index(dd, ng, qB, g0 + t) * SYM_MACRO_PART + rslot;
+      const int q = t - nrow;
+      return D.part + (size_t)macro_index(dd, ng, q, gB) * SYM_MACRO_PART + cslot;
     };
     double ax0 = 0.0, ay0 = 0.0, az0 = 0.0, ax1 = 0.0, ay1 = 0.0, az1 = 0.0;
-    int q = 0;
-    for (; q + 1 < nterm; q += 2) {
-      const double *p0 = slot(q), *p1 = slot(q + 1);
+    int t = 0;
+    for (; t + 1 < nterm; t += 2) {
+      const double *p0 = ptr(t), *p1 = ptr(t + 1);
       ax0 += p0[0]; ay0 += p0[32]; az0 += p0[64];
       ax1 += p1[0]; ay1 += p1[32]; az1 += p1[64];
     }
-    if (q < nterm) {
-      const double *p0 = slot(q);
+    if (t < nterm) {
+      const double *p0 = ptr(t);
       ax0 += p0[0]; ay0 += p0[32]; az0 += p0[64];
     }
     const double ax = ax0 + ax1, ay = ay0 + ay1, az = az0 + az1;
@@ -314,17 +317,15 @@ __global__ void k_reduce_mixed(Dev D, long long npart) {
     if (li >= dd.n || !D.alive[p]) continue;
     const int B = li >> 5, lane = li & 31;
     if (B >= dd.nbm) continue;                  // a block of field particles: kicked by k_field_mixed
+    const int C = SYM_MACRO_COLS, ng = (dd.nbm + C - 1) / C, qB = B >> 2, gB = B / C;
+    const int rslot = (B & 3) * 96 + lane, cslot = 384 + (B % C) * 96 + lane;
     float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-    {
-      const int t0 = row_start(dd, B);
-      for (int J = B; J < dd.nbm; ++J) {
-        const float2 *pp = part + ((size_t)(t0 + (J - B)) * 2 * 3) * 32 + lane;
-        for (int k = 0; k < 3; ++k) { kahan_add(s[k], c[k], pp[32 * k].x); kahan_add(s[k], c[k], -pp[32 * k].y); }
-      }
+    for (int g = (4 / C) * qB; g < ng; ++g) {
+      const float2 *pp = part + (size_t)macro_index(dd, ng, qB, g) * SYM_MACRO_PART + rslot;
+      for (int k = 0; k < 3; ++k) { kahan_add(s[k], c[k], pp[32 * k].x); kahan_add(s[k], c[k], -pp[32 * k].y); }
     }
-    const int Imax = B < dd.nbm ? B : dd.nbm;
-    for (int I = 0; I < Imax; ++I) {
-      const float2 *pp = part + (((size_t)(row_start(dd, I) + (B - I)) * 2 + 1) * 3) * 32 + lane;
+    for (int q = 0; q <= qB; ++q) {
+      const float2 *pp = part + (size_t)macro_index(dd, ng, q, gB) * SYM_MACRO_PART + cslot;
       for (int k = 0; k < 3; ++k) { kahan_add(s[k], c[k], pp[32 * k].x); kahan_add(s[k], c[k], -pp[32 * k].y); }
     }
     const double h = 0.5 * dd.dt;
@@ -472,15 +473,19 @@ __global__ void __launch_bounds__(256) k_energy_pairs(Dev D, int d, unsigned lon
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = warp; t < dd.ntiles; t += nwarps) {
-    const int4 tl = D.tiles[dd.tile_base + t];
-    const int li = tl.y * 32 + lane - dd.off;
+  // every 32 x 32 tile (I, J), I <= J, of the system's macro-tiles: 4 x SYM_MACRO_COLS each
+  for (int t = warp; t < 4 * SYM_MACRO_COLS * dd.ntiles; t += nwarps) {
+    const int4 mt = D.tiles[dd.tile_base + t / (4 * SYM_MACRO_COLS)];
+    const int u = t % (4 * SYM_MACRO_COLS);
+    const int I = mt.y + u / SYM_MACRO_COLS, J = mt.z + u % SYM_MACRO_COLS;
+    if (I >= mt.w || J >= mt.w || J < I) continue;
+    const int li = I * 32 + lane - dd.off;
     const int p = dd.off + li;
     if (li >= dd.nm || li >= dd.n || !D.alive[p]) continue;
     const double xi = D.x[p], yi = D.y[p], zi = D.z[p];
     const double Gmi = __dmul_rn(dd.G, D.m[p]);
     for (int s = 0; s < 32; ++s) {
-      const int lj = tl.z * 32 + s - dd.off;
+      const int lj = J * 32 + s - dd.off;
       if (lj <= li || lj >= dd.n) continue;
       const int q = dd.off + lj;
       if (!D.alive[q]) continue;

@@ -1,18 +1,23 @@
 // The right-angled-trapezoid pair kick (Sec. 2): every pair i < N_m, j > i once, both
 // reactions accumulated, no atomics.
 //
-// Work decomposition.  Indices are cut into 32-blocks; tile (I, J), I <= J, I < ceil(N_m/32),
-// holds the pairs of block I (rows) with block J (columns): the trapezoid becomes a rectangle of
-// off-diagonal tiles plus the diagonal tiles of the triangle, all in one flat list that
-// persistent warps consume in segments from a counter (the fold of the triangle into a
+// Work decomposition.  Indices are cut into 32-blocks; tile (I, J), I <= J, over the column
+// blocks that hold massive bodies, holds the pairs of block I (rows) with block J (columns): the
+// trapezoid becomes a rectangle of off-diagonal tiles plus the diagonal tiles of the triangle.
+// Tiles are grouped into macro-tiles of 4 row blocks (a 128-body quad q) by SYM_MACRO_COLS column
+// blocks (column group p, p >= 4q / SYM_MACRO_COLS), all macro-tiles of all systems in one flat
+// list that persistent CTAs of four warps consume from a counter (the fold of the triangle into a
 // rectangle, done by a work queue instead of index arithmetic).
 //
-// One warp per tile.  Lane l keeps row particle I*32+l in registers; the column particles
+// One CTA per macro-tile, one warp per row block: warp w keeps row particle (4q + w)*32 + l in
+// lane l and sweeps the macro's column blocks in turn; in each tile the column particles
 // rotate through the lanes with warp shuffles (32 steps; 16 on a diagonal tile, where each
 // unordered pair is met once), each carrying its own accumulator, so after the sweep every
-// column accumulator is back in its home lane.  Both sides are written as per-tile partials
-// and summed later in a fixed order: the result does not depend on scheduling, segment length
-// or which other systems share the launch.
+// column accumulator is back in its home lane.  The row accumulators run on across the
+// macro-tile's tiles and are written once per macro-tile; the four warps' column accumulators of
+// each column block are added in shared memory in warp order and written once.  Both kinds of partials are
+// summed later in a fixed order: the result does not depend on scheduling, on how many
+// macro-tiles a CTA takes per grab, or on which other systems share the launch.
 //
 // FP64 path: 16 FP64-pipe instructions per pair (3 differences, 3 for r^2, 2 for r^-3 -- its seed,
 // Newton step and powers run on the integer pipe -- 2 mass scalings, 6 FMAs into the two
@@ -56,37 +61,61 @@ __device__ __forceinline__ bool group_has_pair(const Dev &D, int g, int lo, int 
   return a < D.g_poff[g] + D.g_pcnt[g] && D.gpi[a] == lo && D.gpj[a] == hi;
 }
 
-template <int MODE>
-__device__ __forceinline__ void tile_fp64(const Dev &D, const TileCtx &c, const DiskDesc *dp,
-                                          int t, int4 tl, int lane) {
-  const bool diag = tl.y == tl.z;
-  const int pi = tl.y * 32 + lane;
-  const int li = pi - c.off;
-  const bool live_i = li < c.n && D.alive[pi];
-  const bool row_i = live_i && li < c.nm;
-  const double xi = D.x[pi], yi = D.y[pi], zi = D.z[pi], gmi = D.gm[pi];
-  double axi = 0.0, ayi = 0.0, azi = 0.0;
 
-  int jid = tl.z * 32 + lane;
+// partial slots of macro-tile m: rows [w][component][lane], then columns [k][component][lane]
+__device__ __forceinline__ size_t part_row(int m, int w) { return (size_t)m * SYM_MACRO_PART + w * 96; }
+__device__ __forceinline__ size_t part_col(int m, int k) { return (size_t)m * SYM_MACRO_PART + 384 + k * 96; }
+#define MC SYM_MACRO_COLS
+
+// the row side of one warp: row particle I*32 + lane, its data and its accumulators
+struct RowF64 {
+  int pi;
+  bool live, row;          // a live body; live and massive (a row of the trapezoid)
+  double x, y, z, gm;
+  float xf, yf, zf, vxf, vyf, vzf, lam, sig;   // kick 1: FP32 prefilter copies
+  int gid;                 // kick 2: encounter group
+  double ax, ay, az;       // carried across the macro-tile's column blocks
+};
+
+template <int MODE>
+__device__ __forceinline__ void row_load_fp64(const Dev &D, const TileCtx &c, int I, int lane, RowF64 &r) {
+  r.pi = I * 32 + lane;
+  const int li = r.pi - c.off;
+  r.live = li < c.n && D.alive[r.pi];
+  r.row = r.live && li < c.nm;
+  r.x = D.x[r.pi]; r.y = D.y[r.pi]; r.z = D.z[r.pi]; r.gm = D.gm[r.pi];
+  r.xf = r.yf = r.zf = r.vxf = r.vyf = r.vzf = r.lam = r.sig = 0.f;
+  r.gid = -1;
+  if (MODE == 1) {
+    r.xf = D.xf[r.pi]; r.yf = D.yf[r.pi]; r.zf = D.zf[r.pi];
+    r.vxf = D.vxf[r.pi]; r.vyf = D.vyf[r.pi]; r.vzf = D.vzf[r.pi];
+    r.lam = D.lamf[r.pi]; r.sig = D.sigf[r.pi];
+  } else {
+    r.gid = D.gid[r.pi];
+  }
+  r.ax = r.ay = r.az = 0.0;
+}
+
+// One 32 x 32 tile (rows of block I, columns of block J >= I): both reactions of every pair;
+// the row side goes into r.ax.., the column side comes back in cx, cy, cz (zero on a diagonal
+// tile, whose column side is folded into its rows).
+template <int MODE>
+__device__ __forceinline__ void tile_sweep_fp64(const Dev &D, const TileCtx &c, int sys, RowF64 &r,
+                                                int I, int J, int lane, double &cx, double &cy, double &cz) {
+  const bool diag = I == J;
+  int jid = J * 32 + lane;
   const int lj0 = jid - c.off;
   const bool live_j0 = lj0 < c.n && D.alive[jid];
   int jflags = (live_j0 ? 1 : 0) | ((live_j0 && lj0 < c.nm) ? 2 : 0);
   double xj = D.x[jid], yj = D.y[jid], zj = D.z[jid], gmj = D.gm[jid];
   double axj = 0.0, ayj = 0.0, azj = 0.0;
-
-  // kick 1: FP32 prefilter data; kick 2: group ids
-  float xfi = 0.f, yfi = 0.f, zfi = 0.f, vxfi = 0.f, vyfi = 0.f, vzfi = 0.f, lami = 0.f, sigi = 0.f;
   float xfj = 0.f, yfj = 0.f, zfj = 0.f, vxfj = 0.f, vyfj = 0.f, vzfj = 0.f, lamj = 0.f, sigj = 0.f;
-  int gidi = -1, gidj = -1;
+  int gidj = -1;
   if (MODE == 1) {
-    xfi = D.xf[pi]; yfi = D.yf[pi]; zfi = D.zf[pi];
-    vxfi = D.vxf[pi]; vyfi = D.vyf[pi]; vzfi = D.vzf[pi];
-    lami = D.lamf[pi]; sigi = D.sigf[pi];
     xfj = D.xf[jid]; yfj = D.yf[jid]; zfj = D.zf[jid];
     vxfj = D.vxf[jid]; vyfj = D.vyf[jid]; vzfj = D.vzf[jid];
     lamj = D.lamf[jid]; sigj = D.sigf[jid];
   } else {
-    gidi = D.gid[pi];
     gidj = D.gid[jid];
   }
   const float tauf = __double2float_ru(c.dt);
@@ -114,33 +143,33 @@ __device__ __forceinline__ void tile_fp64(const Dev &D, const TileCtx &c, const 
   for (int s = 0; s < nsteps; ++s) {
     bool valid;
     if (!diag) {
-      valid = row_i && (jflags & 1);
+      valid = r.row && (jflags & 1);
     } else {
-      valid = (jid > pi) ? (row_i && (jflags & 1)) : (live_i && (jflags & 2));
+      valid = (jid > r.pi) ? (r.row && (jflags & 1)) : (r.live && (jflags & 2));
       if (s == 15 && lane >= 16) valid = false;  // pair {l, l+16} belongs to lane l < 16
     }
-    const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    const double dx = xj - r.x, dy = yj - r.y, dz = zj - r.z;
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     const double r3 = rinv3(r2);
     double sj = gmj * r3;
-    double si = gmi * r3;
+    double si = r.gm * r3;
     if (MODE == 1) {
-      const float dxf = xfj - xfi, dyf = yfj - yfi, dzf = zfj - zfi;
+      const float dxf = xfj - r.xf, dyf = yfj - r.yf, dzf = zfj - r.zf;
       const float r2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
-      const float dvxf = vxfj - vxfi, dvyf = vyfj - vyfi, dvzf = vzfj - vzfi;
+      const float dvxf = vxfj - r.vxf, dvyf = vyfj - r.vyf, dvzf = vzfj - r.vzf;
       const float vmag = sqrtf(fmaf(dvzf, dvzf, fmaf(dvyf, dvyf, dvxf * dvxf)));
-      const float Bf = fmaf(tauf, vmag, lami + lamj) * 1.0000039f + 1.9073486e-6f * (sigi + sigj);
+      const float Bf = fmaf(tauf, vmag, r.lam + lamj) * 1.0000039f + 1.9073486e-6f * (r.sig + sigj);
       const bool cand = valid && !(r2f > Bf * Bf);
       if (__any_sync(FULL, cand)) {
         if (cand) {
-          const int lo = min(pi, jid), hi = max(pi, jid);
+          const int lo = min(r.pi, jid), hi = max(r.pi, jid);
           const double ex = __dsub_rn(D.x[hi], D.x[lo]), ey = __dsub_rn(D.y[hi], D.y[lo]),
                        ez = __dsub_rn(D.z[hi], D.z[lo]);
           const double evx = __dsub_rn(D.vx[hi], D.vx[lo]), evy = __dsub_rn(D.vy[hi], D.vy[lo]),
                        evz = __dsub_rn(D.vz[hi], D.vz[lo]);
           const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[lo], D.rh[hi]));
           if (encounter_exact(ex, ey, ez, evx, evy, evz, R0, c.dt)) {
-            const int k = atomicAdd(&D.stat[tl.x].npairs, 1);
+            const int k = atomicAdd(&D.stat[sys].npairs, 1);
             if (k < c.pair_cap) {
               D.raw_i[c.pair_base + k] = lo;
               D.raw_j[c.pair_base + k] = hi;
@@ -153,9 +182,9 @@ __device__ __forceinline__ void tile_fp64(const Dev &D, const TileCtx &c, const 
         }
       }
     } else {
-      if (gidi >= 0 && gidi == gidj && valid) {
-        const int lo = min(pi, jid), hi = max(pi, jid);
-        if (group_has_pair(D, gidi, lo, hi)) {
+      if (r.gid >= 0 && r.gid == gidj && valid) {
+        const int lo = min(r.pi, jid), hi = max(r.pi, jid);
+        if (group_has_pair(D, r.gid, lo, hi)) {
           const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[lo], D.rh[hi]));
           const double w = g0_weight(c, R0, sqrt(r2));
           sj *= w;
@@ -165,30 +194,27 @@ __device__ __forceinline__ void tile_fp64(const Dev &D, const TileCtx &c, const 
     }
     sj = keep_or_zero(sj, valid);
     si = keep_or_zero(si, valid);
-    axi = fma(sj, dx, axi); ayi = fma(sj, dy, ayi); azi = fma(sj, dz, azi);
+    r.ax = fma(sj, dx, r.ax); r.ay = fma(sj, dy, r.ay); r.az = fma(sj, dz, r.az);
     axj = fma(-si, dx, axj); ayj = fma(-si, dy, ayj); azj = fma(-si, dz, azj);
     if (!diag || s + 1 < nsteps) rotate();
   }
-  (void)dp;
-  double *out = D.part + (size_t)t * 2 * 3 * 32 + lane;
   if (diag) {
     const int src = (lane + 16) & 31;
-    axi += __shfl_sync(FULL, axj, src);
-    ayi += __shfl_sync(FULL, ayj, src);
-    azi += __shfl_sync(FULL, azj, src);
-    out[0] = axi; out[32] = ayi; out[64] = azi;
+    r.ax += __shfl_sync(FULL, axj, src);
+    r.ay += __shfl_sync(FULL, ayj, src);
+    r.az += __shfl_sync(FULL, azj, src);
+    cx = 0.0; cy = 0.0; cz = 0.0;
   } else {
-    out[0] = axi; out[32] = ayi; out[64] = azi;
-    out[96] = axj; out[128] = ayj; out[160] = azj;
+    cx = axj; cy = ayj; cz = azj;
   }
 }
 
 // Mixed precision (FP32 pair path): the relative displacement is formed from the two-float split
-// x = xf + xl of each FP64 position, (xf_j - xf_i) + (xl_j - xl_i), which is exact in the high
-// part for nearby bodies and within one FP32 ulp of the rounded FP64 difference otherwise; r^-3
-// from the FP32 rsqrt plus one Newton step; both sides accumulated in FP32 with Kahan
-// compensation and written as (sum, compensation) pairs that the reduction carries into FP64.
-// The encounter check is the same FP64 decision as in the FP64 path.
+// x = xf + xl of each FP64 position, (xf_j - xf_i) + (xl_j - xl_i) -- RN32 of the FP64 difference
+// or a neighbouring float for every pair the level-0 weight does not zero; r^-3 from the FP32
+// rsqrt plus one Newton step; both sides accumulated in FP32 with Kahan compensation and written
+// as (sum, compensation) pairs that the reduction carries into FP64.  The encounter check is the
+// same FP64 decision as in the FP64 path.
 __device__ __forceinline__ void kahan(float &s, float &c, float term) {
   const float y = term - c;
   const float t = s + y;
@@ -196,19 +222,40 @@ __device__ __forceinline__ void kahan(float &s, float &c, float term) {
   s = t;
 }
 
-template <int MODE>
-__device__ __forceinline__ void tile_mixed(const Dev &D, const TileCtx &c, int t, int4 tl, int lane) {
-  const bool diag = tl.y == tl.z;
-  const int pi = tl.y * 32 + lane;
-  const int li = pi - c.off;
-  const bool live_i = li < c.n && D.alive[pi];
-  const bool row_i = live_i && li < c.nm;
-  const float xhi = D.xf[pi], yhi = D.yf[pi], zhi = D.zf[pi];
-  const float xlo = D.xl[pi], ylo = D.yl[pi], zlo = D.zl[pi];
-  const float gmi = D.gmf[pi];
-  float sxi = 0.f, syi = 0.f, szi = 0.f, cxi = 0.f, cyi = 0.f, czi = 0.f;
+struct RowMixed {
+  int pi;
+  bool live, row;
+  float xh, yh, zh, xl, yl, zl, gm;
+  float vxf, vyf, vzf, lam, sig;   // kick 1 prefilter
+  int gid;                         // kick 2
+  float sx, sy, sz, cx, cy, cz;    // Kahan sums of the row side, carried across the macro-tile
+};
 
-  int jid = tl.z * 32 + lane;
+template <int MODE>
+__device__ __forceinline__ void row_load_mixed(const Dev &D, const TileCtx &c, int I, int lane, RowMixed &r) {
+  r.pi = I * 32 + lane;
+  const int li = r.pi - c.off;
+  r.live = li < c.n && D.alive[r.pi];
+  r.row = r.live && li < c.nm;
+  r.xh = D.xf[r.pi]; r.yh = D.yf[r.pi]; r.zh = D.zf[r.pi];
+  r.xl = D.xl[r.pi]; r.yl = D.yl[r.pi]; r.zl = D.zl[r.pi];
+  r.gm = D.gmf[r.pi];
+  r.vxf = r.vyf = r.vzf = r.lam = r.sig = 0.f;
+  r.gid = -1;
+  if (MODE == 1) {
+    r.vxf = D.vxf[r.pi]; r.vyf = D.vyf[r.pi]; r.vzf = D.vzf[r.pi]; r.lam = D.lamf[r.pi]; r.sig = D.sigf[r.pi];
+  } else {
+    r.gid = D.gid[r.pi];
+  }
+  r.sx = r.sy = r.sz = r.cx = r.cy = r.cz = 0.f;
+}
+
+// one tile; the column side comes back as Kahan pairs (s, c) per component, zero on a diagonal
+template <int MODE>
+__device__ __forceinline__ void tile_sweep_mixed(const Dev &D, const TileCtx &c, int sys, RowMixed &r,
+                                                 int I, int J, int lane, float2 &ox, float2 &oy, float2 &oz) {
+  const bool diag = I == J;
+  int jid = J * 32 + lane;
   const int lj0 = jid - c.off;
   const bool live_j0 = lj0 < c.n && D.alive[jid];
   int jflags = (live_j0 ? 1 : 0) | ((live_j0 && lj0 < c.nm) ? 2 : 0);
@@ -216,15 +263,11 @@ __device__ __forceinline__ void tile_mixed(const Dev &D, const TileCtx &c, int t
   float xlj = D.xl[jid], ylj = D.yl[jid], zlj = D.zl[jid];
   float gmj = D.gmf[jid];
   float sxj = 0.f, syj = 0.f, szj = 0.f, cxj = 0.f, cyj = 0.f, czj = 0.f;
-
-  float vxfi = 0.f, vyfi = 0.f, vzfi = 0.f, lami = 0.f, sigi = 0.f;
   float vxfj = 0.f, vyfj = 0.f, vzfj = 0.f, lamj = 0.f, sigj = 0.f;
-  int gidi = -1, gidj = -1;
+  int gidj = -1;
   if (MODE == 1) {
-    vxfi = D.vxf[pi]; vyfi = D.vyf[pi]; vzfi = D.vzf[pi]; lami = D.lamf[pi]; sigi = D.sigf[pi];
     vxfj = D.vxf[jid]; vyfj = D.vyf[jid]; vzfj = D.vzf[jid]; lamj = D.lamf[jid]; sigj = D.sigf[jid];
   } else {
-    gidi = D.gid[pi];
     gidj = D.gid[jid];
   }
   const float tauf = __double2float_ru(c.dt);
@@ -252,35 +295,35 @@ __device__ __forceinline__ void tile_mixed(const Dev &D, const TileCtx &c, int t
   for (int s = 0; s < nsteps; ++s) {
     bool valid;
     if (!diag) {
-      valid = row_i && (jflags & 1);
+      valid = r.row && (jflags & 1);
     } else {
-      valid = (jid > pi) ? (row_i && (jflags & 1)) : (live_i && (jflags & 2));
+      valid = (jid > r.pi) ? (r.row && (jflags & 1)) : (r.live && (jflags & 2));
       if (s == 15 && lane >= 16) valid = false;
     }
-    const float dx = (xhj - xhi) + (xlj - xlo);
-    const float dy = (yhj - yhi) + (ylj - ylo);
-    const float dz = (zhj - zhi) + (zlj - zlo);
+    const float dx = (xhj - r.xh) + (xlj - r.xl);
+    const float dy = (yhj - r.yh) + (ylj - r.yl);
+    const float dz = (zhj - r.zh) + (zlj - r.zl);
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     float ri;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ri) : "f"(r2));
     ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
     const float s3 = ri * ri * ri;
-    float sj = gmj * s3, si = gmi * s3;
+    float sj = gmj * s3, si = r.gm * s3;
     if (MODE == 1) {
-      const float dvxf = vxfj - vxfi, dvyf = vyfj - vyfi, dvzf = vzfj - vzfi;
+      const float dvxf = vxfj - r.vxf, dvyf = vyfj - r.vyf, dvzf = vzfj - r.vzf;
       const float vmag = sqrtf(fmaf(dvzf, dvzf, fmaf(dvyf, dvyf, dvxf * dvxf)));
-      const float Bf = fmaf(tauf, vmag, lami + lamj) * 1.0000039f + 1.9073486e-6f * (sigi + sigj);
+      const float Bf = fmaf(tauf, vmag, r.lam + lamj) * 1.0000039f + 1.9073486e-6f * (r.sig + sigj);
       const bool cand = valid && !(r2 > Bf * Bf * 1.0000153f);
       if (__any_sync(FULL, cand)) {
         if (cand) {
-          const int lo = min(pi, jid), hi = max(pi, jid);
+          const int lo = min(r.pi, jid), hi = max(r.pi, jid);
           const double ex = __dsub_rn(D.x[hi], D.x[lo]), ey = __dsub_rn(D.y[hi], D.y[lo]),
                        ez = __dsub_rn(D.z[hi], D.z[lo]);
           const double evx = __dsub_rn(D.vx[hi], D.vx[lo]), evy = __dsub_rn(D.vy[hi], D.vy[lo]),
                        evz = __dsub_rn(D.vz[hi], D.vz[lo]);
           const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[lo], D.rh[hi]));
           if (encounter_exact(ex, ey, ez, evx, evy, evz, R0, c.dt)) {
-            const int k = atomicAdd(&D.stat[tl.x].npairs, 1);
+            const int k = atomicAdd(&D.stat[sys].npairs, 1);
             if (k < c.pair_cap) {
               D.raw_i[c.pair_base + k] = lo;
               D.raw_j[c.pair_base + k] = hi;
@@ -293,9 +336,9 @@ __device__ __forceinline__ void tile_mixed(const Dev &D, const TileCtx &c, int t
         }
       }
     } else {
-      if (gidi >= 0 && gidi == gidj && valid) {
-        const int lo = min(pi, jid), hi = max(pi, jid);
-        if (group_has_pair(D, gidi, lo, hi)) {
+      if (r.gid >= 0 && r.gid == gidj && valid) {
+        const int lo = min(r.pi, jid), hi = max(r.pi, jid);
+        if (group_has_pair(D, r.gid, lo, hi)) {
           const double R0 = __dmul_rn(c.lam, __dadd_rn(D.rh[lo], D.rh[hi]));
           const double ex = D.x[hi] - D.x[lo], ey = D.y[hi] - D.y[lo], ez = D.z[hi] - D.z[lo];
           const float w = (float)g0_weight(c, R0, sqrt(fma(ez, ez, fma(ey, ey, ex * ex))));
@@ -305,65 +348,124 @@ __device__ __forceinline__ void tile_mixed(const Dev &D, const TileCtx &c, int t
       }
     }
     if (!valid) { sj = 0.f; si = 0.f; }
-    kahan(sxi, cxi, sj * dx); kahan(syi, cyi, sj * dy); kahan(szi, czi, sj * dz);
+    kahan(r.sx, r.cx, sj * dx); kahan(r.sy, r.cy, sj * dy); kahan(r.sz, r.cz, sj * dz);
     kahan(sxj, cxj, -si * dx); kahan(syj, cyj, -si * dy); kahan(szj, czj, -si * dz);
     if (!diag || s + 1 < nsteps) rotate();
   }
-  float2 *out = reinterpret_cast<float2 *>(D.part) + (size_t)t * 2 * 3 * 32 + lane;
   if (diag) {
     const int src = (lane + 16) & 31;
     const float hx = __shfl_sync(FULL, sxj, src), hy = __shfl_sync(FULL, syj, src), hz = __shfl_sync(FULL, szj, src);
     const float kx = __shfl_sync(FULL, cxj, src), ky = __shfl_sync(FULL, cyj, src), kz = __shfl_sync(FULL, czj, src);
-    kahan(sxi, cxi, hx); kahan(sxi, cxi, -kx);
-    kahan(syi, cyi, hy); kahan(syi, cyi, -ky);
-    kahan(szi, czi, hz); kahan(szi, czi, -kz);
-    out[0] = make_float2(sxi, cxi); out[32] = make_float2(syi, cyi); out[64] = make_float2(szi, czi);
+    kahan(r.sx, r.cx, hx); kahan(r.sx, r.cx, -kx);
+    kahan(r.sy, r.cy, hy); kahan(r.sy, r.cy, -ky);
+    kahan(r.sz, r.cz, hz); kahan(r.sz, r.cz, -kz);
+    ox = make_float2(0.f, 0.f); oy = ox; oz = ox;
   } else {
-    out[0] = make_float2(sxi, cxi); out[32] = make_float2(syi, cyi); out[64] = make_float2(szi, czi);
-    out[96] = make_float2(sxj, cxj); out[128] = make_float2(syj, cyj); out[160] = make_float2(szj, czj);
+    ox = make_float2(sxj, cxj); oy = make_float2(syj, cyj); oz = make_float2(szj, czj);
+  }
+}
+
+// One CTA (four warps) per macro-tile.  The macro-tile list entry is {system, first row block,
+// first column block, end of the system's massive blocks}; warp w takes row block I0 + w and
+// sweeps column blocks J0..J0+SYM_MACRO_COLS-1, skipping those below its row (the triangle) or
+// past the massive blocks.  Rows are written once per macro-tile, columns after the four warps' sums for
+// each column block are added in warp order through shared memory.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_trap_fp64(Dev D) {
+  __shared__ double colbuf[4][MC][3][32];     // [warp][column block][component][lane]
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nmac = D.ntiles_total;
+  const int S = D.seg_len;
+  int *counter = &D.work[MODE - 1];
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  int m0 = s_item * S;
+  while (m0 < nmac) {
+    const int m1 = min(m0 + S, nmac);
+    for (int m = m0; m < m1; ++m) {
+      const int4 mt = D.tiles[m];
+      const TileCtx c = load_ctx(&D.disks[mt.x]);
+      const int I = mt.y + w;
+      const bool has_row = I < mt.w;
+      RowF64 r;
+      if (has_row) row_load_fp64<MODE>(D, c, I, lane, r);
+#pragma unroll 1
+      for (int k = 0; k < MC; ++k) {
+        const int J = mt.z + k;
+        double cx = 0.0, cy = 0.0, cz = 0.0;
+        if (has_row && J < mt.w && J >= I) tile_sweep_fp64<MODE>(D, c, mt.x, r, I, J, lane, cx, cy, cz);
+        colbuf[w][k][0][lane] = cx; colbuf[w][k][1][lane] = cy; colbuf[w][k][2][lane] = cz;
+      }
+      double *rowp = D.part + part_row(m, w) + lane;
+      rowp[0] = has_row ? r.ax : 0.0; rowp[32] = has_row ? r.ay : 0.0; rowp[64] = has_row ? r.az : 0.0;
+      __syncthreads();
+      if (w < MC) {                                             // warp w adds column block w
+        double *colp = D.part + part_col(m, w) + lane;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          colp[32 * q] = ((colbuf[0][w][q][lane] + colbuf[1][w][q][lane]) + colbuf[2][w][q][lane]) + colbuf[3][w][q][lane];
+      }
+      // the next item is taken while the columns are added (everyone has read s_item)
+      if (m + 1 == m1 && threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+      __syncthreads();                        // colbuf is free, s_item is current
+    }
+    m0 = s_item * S;
   }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_trap_mixed(Dev D) {
-  const int lane = threadIdx.x & 31;
-  const int ntiles = D.ntiles_total;
+  __shared__ float2 colbuf[4][MC][3][32];
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nmac = D.ntiles_total;
   const int S = D.seg_len;
   int *counter = &D.work[MODE - 1];
-  for (;;) {
-    int seg = 0;
-    if (lane == 0) seg = atomicAdd(counter, 1);
-    seg = __shfl_sync(FULL, seg, 0);
-    const int t0 = seg * S;
-    if (t0 >= ntiles) break;
-    const int t1 = min(t0 + S, ntiles);
-    for (int t = t0; t < t1; ++t) {
-      const int4 tl = D.tiles[t];
-      const TileCtx c = load_ctx(&D.disks[tl.x]);
-      tile_mixed<MODE>(D, c, t, tl, lane);
+  float2 *part = reinterpret_cast<float2 *>(D.part);
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  int m0 = s_item * S;
+  while (m0 < nmac) {
+    const int m1 = min(m0 + S, nmac);
+    for (int m = m0; m < m1; ++m) {
+      const int4 mt = D.tiles[m];
+      const TileCtx c = load_ctx(&D.disks[mt.x]);
+      const int I = mt.y + w;
+      const bool has_row = I < mt.w;
+      RowMixed r;
+      if (has_row) row_load_mixed<MODE>(D, c, I, lane, r);
+#pragma unroll 1
+      for (int k = 0; k < MC; ++k) {
+        const int J = mt.z + k;
+        float2 ox = make_float2(0.f, 0.f), oy = ox, oz = ox;
+        if (has_row && J < mt.w && J >= I) tile_sweep_mixed<MODE>(D, c, mt.x, r, I, J, lane, ox, oy, oz);
+        colbuf[w][k][0][lane] = ox; colbuf[w][k][1][lane] = oy; colbuf[w][k][2][lane] = oz;
+      }
+      float2 *rowp = part + part_row(m, w) + lane;
+      const float2 z = make_float2(0.f, 0.f);
+      rowp[0] = has_row ? make_float2(r.sx, r.cx) : z;
+      rowp[32] = has_row ? make_float2(r.sy, r.cy) : z;
+      rowp[64] = has_row ? make_float2(r.sz, r.cz) : z;
+      __syncthreads();
+      if (w < MC) {
+        float2 *colp = part + part_col(m, w) + lane;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float s = 0.f, cc = 0.f;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float2 t = colbuf[v][w][q][lane];
+            kahan(s, cc, t.x);
+            kahan(s, cc, -t.y);
+          }
+          colp[32 * q] = make_float2(s, cc);
+        }
+      }
+      if (m + 1 == m1 && threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+      __syncthreads();
     }
-  }
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(128) k_trap_fp64(Dev D) {
-  const int lane = threadIdx.x & 31;
-  const int ntiles = D.ntiles_total;
-  const int S = D.seg_len;
-  int *counter = &D.work[MODE - 1];
-  for (;;) {
-    int seg = 0;
-    if (lane == 0) seg = atomicAdd(counter, 1);
-    seg = __shfl_sync(FULL, seg, 0);
-    const int t0 = seg * S;
-    if (t0 >= ntiles) break;
-    const int t1 = min(t0 + S, ntiles);
-    for (int t = t0; t < t1; ++t) {
-      const int4 tl = D.tiles[t];
-      const DiskDesc *dp = &D.disks[tl.x];
-      const TileCtx c = load_ctx(dp);
-      tile_fp64<MODE>(D, c, dp, t, tl, lane);
-    }
+    m0 = s_item * S;
   }
 }
 

@@ -55,7 +55,20 @@ def test_status_strings(built_lib):
 def test_footprint_grows_with_size(built_lib):
     import paper_2304_07325_gb300 as sy
     a, b = sy.Pool.footprint(1000, 1000), sy.Pool.footprint(10000, 10000)
-    assert 0 < a < b and b > 70e6      # ~49k tiles of 1.5 KiB of partials at N = 10,000
+    # N = 10,000: 313 massive blocks, ~6,300 macro-tiles of 4 x 2 tiles, 4.5 KiB of partials each
+    assert 0 < a < b and 20e6 < b < 60e6
+
+
+def test_macro_tile_capacity_bound():
+    """The pool allocates partials for T / (4 C) + sqrt(2T) + 2 macro-tiles per system of T tiles
+    (C column blocks per macro-tile): that must cover the macro-tiles of every block count."""
+    import math
+    for C in (2, 4):
+        for nbm in range(1, 20001):
+            T = nbm * (nbm + 1) // 2
+            nq, ng = (nbm + 3) // 4, (nbm + C - 1) // C
+            M = nq * ng - (4 // C) * nq * (nq - 1) // 2
+            assert M <= T // (4 * C) + math.ceil(math.sqrt(2 * T)) + 2, (C, nbm)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

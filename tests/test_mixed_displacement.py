@@ -93,5 +93,7 @@ def test_the_kernels_use_this_expression():
     trap = open(os.path.join(CSRC, "k_trap.cu")).read()
     misc = open(os.path.join(CSRC, "k_misc.cu")).read()
     for c in "xyz":
-        assert f"const float d{c} = ({c}hj - {c}hi) + ({c}lj - {c}lo);" in trap
+        # the trapezoid tiles (row r, column j) and the field rectangle (source q, field particle p)
+        assert f"const float d{c} = ({c}hj - r.{c}h) + ({c}lj - r.{c}l);" in trap
+        assert f"const float d{c} = (q.{c}f - {c}hp) + (q.{c}l - {c}lp);" in trap
         assert f"D.{c}l[p] = __double2float_rn({c} - (double)f{c});" in misc
