@@ -40,7 +40,7 @@ BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
 # DRAM read + write per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, N = 10,000, FP64)
 # of the current kernels; None until a capture of the current kernel is on record
 RECURSION_TRAFFIC_BYTES = 1987840 + 21248      # first step of the disk (profiles/k_recursion_fp64_fit.md)
-KICK_TRAFFIC_BYTES = ((1841920 + 13689600) + (1404416 + 11892992)) / 2   # kick 1, kick 2 (profiles/k_trap_fp64_disk_N10000.md)
+KICK_TRAFFIC_BYTES = ((1149184 + 0) + (879360 + 0)) / 2        # kick 1, kick 2 (profiles/k_trap_fp64_disk_N10000.md)
 # Step size at which the batched and served forms and the one-at-a-time form all keep the energy
 # error of every merger-free disk below 1e-10 (measured on the 64 batched disks: 5.7e-11 after 20
 # steps at 0.125 yr, 1.1e-10 at 0.2, 5.2e-10 at 0.5)
@@ -657,7 +657,7 @@ def run_ours(args):
         roofline_kick = {"kernel": "k_trap_fp64 (trapezoid pair kick)", "bound": "alu", "achieved": kick_tflops,
                          "peak": fp64_tflops, "unit": "TFLOP/s", "frac": kick_tflops / fp64_tflops,
                          "traffic": KICK_TRAFFIC_BYTES if traffic_ok else None,
-                         "algorithmic_bytes": 32 * (args.n + args.n_field) + 48 * (args.n + args.n_field),
+                         "algorithmic_bytes": 32 * args.n + 48 * args.n,
                          "ms_per_launch": kick_ms, "flops_per_pair": FLOPS_PER_PAIR_KICK,
                          "peak_source": "measured by symba_measure_rates in this run (FP64 FMAs on every SM)"}
         phases = {name: phase_tot[i] / args.steps for i, name in enumerate(sy.PHASES)}
