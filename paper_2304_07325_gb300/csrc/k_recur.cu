@@ -481,11 +481,15 @@ __device__ __forceinline__ double csum3(double p, int base) {
 // The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
 // FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
 // e = 1 - r2 t still reach full FP64 accuracy.  false when r2e is not a normal FP32 number.
-__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok, float &y0f) {
+// The FP32 seed alone: y0f ~ 1/sqrt(r2e), ok when r2e is a normal FP32 number.
+__device__ __forceinline__ void seed_f32(float r2e, bool &ok, float &y0f) {
   const unsigned yb = __float_as_uint(r2e);
   const int fe = (int)((yb >> 23) & 0xFF);
   ok = fe >= 1 && fe <= 253 && (int)yb > 0;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(ok ? r2e : 1.0f));
+}
+__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok, float &y0f) {
+  seed_f32(r2e, ok, y0f);
   const unsigned b = __float_as_uint(y0f);
   const int ey = (int)((b >> 23) & 0xFF);
   y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
@@ -495,6 +499,14 @@ __device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &
   const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
   const long long e2 = 2 * (ey - 127) + top + 1023;
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+}
+// The double equal to a normal FP32 value, built on the integer pipe (a conversion instruction
+// takes the FP64 pipe's rate); FP32 zeros and subnormals give zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return e == 0u ? 0.0 : __hiloint2double((int)hi, (int)(b << 29));
 }
 __device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok) {
   float y0f;
@@ -551,7 +563,7 @@ __device__ __forceinline__ double rinv3_est(double r2, float r2e, double &t, dou
 // per-level constants of the single-pair path, cached in shared memory
 enum {
   LC_H, LC_HH, LC_T2, LC_R2, LC_A1, LC_B1, LC_A2, LC_B2, LC_GHA, LC_GHB, LC_T3, LC_MUNH, LC_H15,
-  LC_MUNH15, LC_R2N, LC_R2P, LC_N
+  LC_R2N, LC_R2P, LC_N
 };
 
 // Runs the sub-steps of levels >= k with F_{k-1} = {q}, from the opening of a sub-step at level
@@ -597,7 +609,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
 
   // current level's constants
   // (h^2, h^3 and 1.5 h serve only the order-3 drift, which reads them from the cache)
-  double h, hh, R2, A1, B1, A2, B2, ghs, munh, munh15, R2n, R2p;
+  double h, hh, R2, A1, B1, A2, B2, ghs, munh, R2n, R2p;
   float hf, R2f;
   auto set_level = [&](int jj) {
     double *Lc = lc + LC_N * jj;
@@ -618,7 +630,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       const double v[LC_N] = {hj, hh_, t2_, cpy(s1, lane, 2), cpy(s2, lane, 0), -cpy(s2, lane, 1),
                               cpy(s2, lane, 2), -cpy(s2, lane, 3), cpy(s3, lane, 0),
                               cpy(s3, lane, 1), cpy(s3, lane, 2), cpy(s3, lane, 3), cpy(s4, lane, 1),
-                              cpy(s3, lane, 3) * 1.5, cpy(s1, lane, 3), cpy(s4, lane, 2)};
+                              cpy(s1, lane, 3), cpy(s4, lane, 2)};
 #pragma unroll
       for (int i = 0; i < LC_N; ++i) Lc[i] = v[i];
       have |= 1ull << jj;
@@ -627,7 +639,6 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     A1 = Lc[LC_A1]; B1 = Lc[LC_B1]; A2 = Lc[LC_A2]; B2 = Lc[LC_B2];
     ghs = flip(Lc[pb ? LC_GHA : LC_GHB], sgn_b);       // -G m_a h/2 on body b, G m_b h/2 on a
     munh = Lc[LC_MUNH];
-    munh15 = Lc[LC_MUNH15];
     R2n = Lc[LC_R2N]; R2p = Lc[LC_R2P];
     hf = f32_trunc(h);
     R2f = f32_trunc(R2) * (1.0f + 3.0517578e-5f);     // not below R2
@@ -805,6 +816,29 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     rb_ok = __all_sync(FULL, ok);
   };
   auto rb3_nb = [&]() { rb3 = fma(rbty, rbe * fma(rbe, 1.875, 1.5), rbty); };
+  // the FP32 part of body_r_nb() alone: the copies of x and the seed 1/|x| the FP32 decisions use
+  auto body_f32 = [&]() {
+    const float xf = f32_trunc(X);
+    bx0 = __shfl_sync(FULL, xf, base);
+    bx1 = __shfl_sync(FULL, xf, base + 1);
+    bx2 = __shfl_sync(FULL, xf, base + 2);
+    bool ok;
+    seed_f32(fmaf(bx2, bx2, fmaf(bx1, bx1, bx0 * bx0)), ok, brif);
+    rb_ok = __all_sync(FULL, ok);
+  };
+  // 1/r^3 of this lane's body, carried along the common sub-steps: a common sub-step drifts by
+  // the order-2 series, which moves r^2 by the factor 1 + u with
+  //   u = 2 h (x.v)/r^2 + h^2 (v^2/r^2 - mu/r^3)  (+ h^3 mu (x.v)/r^5 and smaller),
+  // so 1/r^3 moves by (1 + u)^(-3/2) = 1 - 3u/2 + 15u^2/8 (+ O(u^3)).  The order-2 regime bounds
+  // h^2 max(mu/r^3, ((x.v)/r^2)^2, |v^2/r^2 - mu/r^3|) by 5e-13, so |u| < 2e-6, the dropped
+  // terms are below 1e-18, and the FP32 evaluation of u from the decisions' truncated copies
+  // errs by at most ~1e-12 (2^-39.7) relative per sub-step.  After GC_MAX carried sub-steps
+  // (2^-35.7 at most) 1/r^3 is formed again in full.  f' = -mu h/r^3 enters v' as f' x, which
+  // in the order-2 regime is below 7e-7 of v on a bound orbit, so the carried factor moves v
+  // by less than 2^-56 of v.
+  constexpr int GC_MAX = 16;
+  double rb3c = 0.0;
+  int gc_n = GC_MAX;            // carried sub-steps since 1/r^3 was formed; GC_MAX: not valid
 
   // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
   // drift_series): 2, 3, 6, or 9 for the Kepler solver
@@ -823,7 +857,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
   };
   // the same decision from the FP32 copies and the seed body_r_nb() took (valid when rb_ok)
-  auto drift_order_nb = [&]() -> unsigned {
+  auto drift_order_nb = [&](float &pfo, float &qfo) -> unsigned {
     const float vf = f32_trunc(V);
     const float v0 = __shfl_sync(FULL, vf, base), v1 = __shfl_sync(FULL, vf, base + 1);
     const float v2f = __shfl_sync(FULL, vf, base + 2);
@@ -832,6 +866,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float ri2f = brif * brif;
     const float uf = muf * ri2f * brif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
+    pfo = pf;
+    qfo = qf;
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
   };
 
@@ -910,23 +946,27 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       V = fma(hc, d, V);                   // opening kick (hc = 0 when the weight vanishes)
       bool fl = lt_nn(r2, R2);             // inside R_j: the pair is in F_j
       if (!fl) {
-        // one straight block: distances from the sun, the FP32 decisions and the order-2 drift
-        // they usually select
-        body_r_nb();
+        // one straight block: the FP32 decisions and the order-2 drift they usually select, with
+        // 1/r^3 carried (rb3c); when it is not valid, the sub-step takes the forms below
+        body_f32();
         const bool far = far_apart(U);
-        unsigned ord = drift_order_nb();
-        // the order-2 drift as in drift(2), with f' = -mu h/r^3 straight from the seed terms,
-        // y0^3 (1 + 3e/2) (-mu h): the series' next term, 15/8 e^2 < 2^-42, is dropped -- in the
-        // order-2 regime f' x is below 1e-6 of v (h n < 1e-6), so it moves v by < 2^-62 of v
-        const double fd = rbty * fma(rbe, munh15, munh);
+        float pf, qf;
+        unsigned ord = drift_order_nb(pf, qf);
+        // the order-2 drift as in drift(2), f' = -mu h/r^3
+        const double fd = munh * rb3c;
         const double W = fma(fd, X, V), Y = fma(hh, V, X);
         const double Xn = fma(hh, W, Y);
         const double Vn = fma(fd, Y, V);
-        if (far && ord == 2u && rb_ok) {
+        // (1 + u)^(-3/2) - 1 for this drift (valid with the order-2 series and rb_ok)
+        const float u = fmaf(2.0f * hf, pf, hf * hf * qf);
+        const double dr3 = f32_to_f64(u * fmaf(1.875f, u, -1.5f));
+        if (far && ord == 2u && rb_ok && gc_n < GC_MAX) {
           // the common sub-step: F_j stays empty, series of order 2, closing force and kick
           plev = j - 1;
           X = Xn;
           V = Vn;
+          rb3c = fma(rb3c, dr3, rb3c);
+          ++gc_n;
           sep();
           const double Vk = V;
           forces_nb();
@@ -939,11 +979,19 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           if (++cj < cM) continue;
           level_done = true;
         } else {
+          // 1/r^3 in full; an order-2 drift from here starts a new carried run
+          const bool fresh = far && ord == 2u && rb_ok;
           if (rb_ok) {
+            body_r_nb();
             rb3_nb();
           } else {
             body_r();
             ord = drift_order();
+          }
+          gc_n = GC_MAX;
+          if (fresh) {
+            rb3c = fma(rb3, dr3, rb3);
+            gc_n = 0;
           }
           if (far && ord <= 3u) {
             plev = j - 1;
@@ -979,6 +1027,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         if (lane == 0) set_status(&D.stat[cd], SYMBA_E_DEPTH);
         body_r();
         drift(drift_order());
+        gc_n = GC_MAX;
         sep();
         start = false;
       }
