@@ -833,10 +833,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   // h^2 max(mu/r^3, ((x.v)/r^2)^2, |v^2/r^2 - mu/r^3|) by 5e-13, so |u| < 2e-6, the dropped
   // terms are below 1e-18, and the FP32 evaluation of u from the decisions' truncated copies
   // errs by at most ~1e-12 (2^-39.7) relative per sub-step.  After GC_MAX carried sub-steps
-  // (2^-35.7 at most) 1/r^3 is formed again in full.  f' = -mu h/r^3 enters v' as f' x, which
+  // (2^-34.7 at most) 1/r^3 is formed again in full.  f' = -mu h/r^3 enters v' as f' x, which
   // in the order-2 regime is below 7e-7 of v on a bound orbit, so the carried factor moves v
-  // by less than 2^-56 of v.
-  constexpr int GC_MAX = 16;
+  // by less than 2^-55 of v.
+  constexpr int GC_MAX = 32;
   double rb3c = 0.0;
   int gc_n = GC_MAX;            // carried sub-steps since 1/r^3 was formed; GC_MAX: not valid
 
