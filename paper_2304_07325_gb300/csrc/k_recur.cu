@@ -651,9 +651,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   bool rcache = false;          // c_ri, c_ri3 hold 1/r and 1/r^3 of the current positions
   int c_lvl = -1;               // level of the last force at these positions, its weight c_f,
   bool c_inner = false;         // and whether that weight was g (inside R_level, non-zero)
-  auto sep = [&]() {
+  // (Xo: the other body's x in this lane's copy and component)
+  auto sep2 = [&](double Xo) {
     // x_b - x_a on both bodies' lanes as a sum of sign-flipped operands (exactly X - Xo, Xo - X)
-    const double Xo = __shfl_xor_sync(FULL, X, 4);
     d = flip(X, sgn_a) + flip(Xo, sgn_b);
     const float df = f32_trunc(d);
     const float a = __shfl_sync(FULL, df, base), b = __shfl_sync(FULL, df, base + 1);
@@ -663,6 +663,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     r2f = f32_trunc(r2);
     rcache = false;
   };
+  auto sep = [&]() { sep2(__shfl_xor_sync(FULL, X, 4)); };
 
   // level-j force: hc = (h/2) w_j(r) G m_other / r^3 with this body's sign, zero when w_j
   // vanishes (fz: outside [R_{j+1}, R_{j-1})).  Branch-free, so that it schedules together with
@@ -952,11 +953,15 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         const bool far = far_apart(U);
         float pf, qf;
         unsigned ord = drift_order_nb(pf, qf);
-        // the order-2 drift as in drift(2), f' = -mu h/r^3
+        // the order-2 drift as in drift(2), f' = -mu h/r^3, in two FP64 instructions: copies 0-1
+        // form W = f' x + v and then x' = h/2 W + Y, copies 2-3 Y = h/2 v + x and then
+        // v' = f' Y + v (the same operations as drift(2), so the same results)
         const double fd = munh * rb3c;
-        const double W = fma(fd, X, V), Y = fma(hh, V, X);
-        const double Xn = fma(hh, W, Y);
-        const double Vn = fma(fd, Y, V);
+        const double s_wy = fma_rn(bsel(hh, fd, m1), bsel(V, X, m1), bsel(X, V, m1));
+        const double W = cpy(s_wy, lane, 0), Y = cpy(s_wy, lane, 2);
+        const double s_xv = fma_rn(bsel(fd, hh, m1), bsel(Y, W, m1), bsel(V, Y, m1));
+        const double Xn = cpy(s_xv, lane, 0), Vn = cpy(s_xv, lane, 2);
+        const double Xno = __shfl_sync(FULL, s_xv, (lane & 7) ^ 4);     // the other body's x'
         // (1 + u)^(-3/2) - 1 for this drift (valid with the order-2 series and rb_ok)
         const float u = fmaf(2.0f * hf, pf, hf * hf * qf);
         const double dr3 = f32_to_f64(u * fmaf(1.875f, u, -1.5f));
@@ -967,7 +972,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           V = Vn;
           rb3c = fma(rb3c, dr3, rb3c);
           ++gc_n;
-          sep();
+          sep2(Xno);
           const double Vk = V;
           forces_nb();
           V = fma(hc, d, Vk);
