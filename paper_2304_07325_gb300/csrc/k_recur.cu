@@ -651,6 +651,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   bool rcache = false;          // c_ri, c_ri3 hold 1/r and 1/r^3 of the current positions
   int c_lvl = -1;               // level of the last force at these positions, its weight c_f,
   bool c_inner = false;         // and whether that weight was g (inside R_level, non-zero)
+  bool c_outer = false;         // or 1 - g of the level above (outside R_level, non-zero)
   // (Xo: the other body's x in this lane's copy and component)
   auto sep2 = [&](double Xo) {
     // x_b - x_a on both bodies' lanes as a sum of sign-flipped operands (exactly X - Xo, Xo - X)
@@ -683,9 +684,24 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       // entering level j at the positions of the last level-(j-1) force, with the pair between
       // R_j and R_{j-1}: the weights telescope, w_j = 1 - g_{j-1}(r) = 1 - w_{j-1} (the same
       // argument (r - R_j) / (R_{j-1} - R_j) in both), so only the products remain
-      hc = (1.0 - c_f) * (c_ri3 * g);
+      const double wt = 1.0 - c_f;
+      hc = wt * (c_ri3 * g);
+      c_f = wt;
       c_lvl = j;
       c_inner = false;
+      c_outer = true;
+      return;
+    }
+    if (rcache && c_lvl == j + 1 && c_outer && inner && !fz) {
+      // back at level j at the positions of the last level-(j+1) force, with the pair between
+      // R_{j+1} and R_j: w_j = g_j(r) = 1 - w_{j+1} (the same argument (r - R_{j+1}) /
+      // (R_j - R_{j+1}) in both)
+      const double wt = 1.0 - c_f;
+      hc = wt * (c_ri3 * g);
+      c_f = wt;
+      c_lvl = j;
+      c_inner = true;
+      c_outer = false;
       return;
     }
     // 1/r and 1/r^3 are level-independent: on entering a deeper level at unchanged positions
@@ -713,6 +729,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     c_f = w;
     c_lvl = j;
     c_inner = inner && !fz;
+    c_outer = !inner && !fz;
   };
   // the same for the straight block: no branch; f_ok = false when the seed was out of range
   bool f_ok = true;
@@ -742,6 +759,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     c_f = w;
     c_lvl = j;
     c_inner = inner && !fz;
+    c_outer = !inner && !fz;
     rcache = f_ok;
   };
   auto forces_skip = [&]() {
