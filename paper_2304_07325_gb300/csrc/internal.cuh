@@ -620,9 +620,14 @@ __device__ __forceinline__ bool drift_series(double mu, double t, double &x, dou
   const double u = mu * ri2 * ri;
   const double t2 = t * t;
   const double x0 = x, y0 = y, z0 = z;
+  // In v' the term f' x is already ~x of v (x = n t), so f' needs one order more than f, g and
+  // g': (3/2) u p t^2 at order 2 (up to 1.5 x^2 of v, 7e-13) and (3uq - 15up^2 + u^2) t^3/6 at
+  // order 3 (up to 3.3e-14 of v).  Their size lets FP32 (the decision's u, p, q) supply them.
   if (sf < 5e-13f) {
-    // x < 1e-6: terms of order x^3 and beyond are below 1e-18
-    const double fm1 = t2 * (-0.5 * u), fd = -u * t;
+    // x < 1e-6: f - 1, g, g' - 1 to order t^2, f' = -u t (1 - 3/2 p t) to t^2; the rest of the
+    // series moves x' and v' by a few 1e-18 at most
+    const double fm1 = t2 * (-0.5 * u), fd0 = -u * t;
+    const double fd = fma(fd0, (double)(-1.5f * pf * tf), fd0);
     x = fma(fm1, x0, fma(t, vx, x0));
     y = fma(fm1, y0, fma(t, vy, y0));
     z = fma(fm1, z0, fma(t, vz, z0));
@@ -634,11 +639,13 @@ __device__ __forceinline__ bool drift_series(double mu, double t, double &x, dou
   const double p = fma(z, vz, fma(y, vy, x * vx)) * ri2;
   double fm1, gmt, fd, gdm1;
   if (sf < 5e-10f) {
-    // x < 3.2e-5: terms of order x^4 and beyond are below 1.1e-18
+    // x < 3.2e-5: f - 1, g, g' - 1 to order t^3, f' to t^3 (its t^3 term, (3uq - 15up^2 + u^2)
+    // t^3/6, in FP32); the rest of the series moves x' and v' by a few 1e-18 at most
     const double up = u * p;
     fm1 = t2 * fma(t, 0.5 * up, -0.5 * u);
     gmt = t2 * t * (-u * (1.0 / 6.0));
-    fd = t * fma(t, 1.5 * up, -u);
+    fd = t * fma(t, 1.5 * up, -u) +
+         (double)((3.0f * uf * qf - 15.0f * uf * pf * pf + uf * uf) * (1.0f / 6.0f) * tf * tf * tf);
     gdm1 = t2 * fma(t, up, -0.5 * u);
   } else {
     const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));

@@ -859,6 +859,10 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
   double rb3c = 0.0;
   int gc_n = GC_MAX;            // carried sub-steps since 1/r^3 was formed; GC_MAX: not valid
 
+  // u = mu/r^3, p = (x.v)/r^2 and q = v^2/r^2 - u of this lane's body in FP32, from the last
+  // order decision: the drift series take from them the terms whose size bounds their needed
+  // precision far below FP32's (f' (3/2) p h for order 2, the t^3 term of f' for order 3)
+  float ds_u = 0.0f, ds_p = 0.0f, ds_q = 0.0f;
   // order of the drift series for both bodies over h, from FP32 copies (the thresholds of
   // drift_series): 2, 3, 6, or 9 for the Kepler solver
   auto drift_order = [&]() -> unsigned {
@@ -873,6 +877,9 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float rif = rsqrtf(rrf), ri2f = rif * rif;
     const float uf = muf * ri2f * rif, pf = rvf * ri2f, qf = fmaf(vvf, ri2f, -uf);
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
+    ds_u = uf;
+    ds_p = pf;
+    ds_q = qf;
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
   };
   // the same decision from the FP32 copies and the seed body_r_nb() took (valid when rb_ok)
@@ -887,17 +894,22 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     const float so = fmaxf(fmaxf(uf, pf * pf), fabsf(qf)) * hf * hf;
     pfo = pf;
     qfo = qf;
+    ds_u = uf;
+    ds_p = pf;
+    ds_q = qf;
     return __reduce_max_sync(FULL, !(so <= 2.0e-6f) ? 9u : (so < 5e-13f ? 2u : (so < 5e-10f ? 3u : 6u)));
   };
 
   // Kepler drift of both bodies over h: Lagrange series of order 2 or 3, else the scalar path
   auto drift = [&](unsigned ord) {
     if (ord == 2u) {
-      // f - 1 = f' h/2 with f' = -mu h/r^3: x' = (x + h/2 v) + h/2 (v + f' x), v' = v + f' (x + h/2 v)
+      // f - 1 = f' h/2 with f' = -mu h/r^3: x' = (x + h/2 v) + h/2 (v + f' x), v' = v + f'' Y with
+      // f'' = f' (1 - 3/2 p h), the series' f' to second order (a term of up to 1e-6 of f', which
+      // moves v by up to 7e-13 of v; its FP32 evaluation errs by < 1e-18 of v)
       const double fd = munh * rb3;
       const double W = fma(fd, X, V), Y = fma(hh, V, X);
       X = fma(hh, W, Y);
-      V = fma(fd, Y, V);
+      V = fma(fma(fd, f32_to_f64(-1.5f * hf * ds_p), fd), Y, V);
     } else if (ord == 3u) {
       const double X1 = fma(h, V, X);
       const double rv = csum3(X * V, base);
@@ -912,8 +924,12 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
       const double t2 = Lc[LC_T2], t3 = Lc[LC_T3], h15 = Lc[LC_H15];
       const double s4 = fma4(m0, m1, hh, up, nhu, h15, up, -u, h, up, nhu, t3, nu6, -0.0);
       // [f - 1 | f' | g' - 1 | x + h v + (g - h) v]
-      const double s5 = fma4(m0, m1, t2, cpy(s4, lane, 0), -0.0, h, cpy(s4, lane, 1), -0.0,
-                             t2, cpy(s4, lane, 2), -0.0, cpy(s4, lane, 3), V, X1);
+      // f' to third order: + (3uq - 15up^2 + u^2) h^3/6, below 3.3e-14 of v in the order-3 regime,
+      // so its FP32 evaluation suffices
+      const float hk3 = (3.0f * ds_u * ds_q - 15.0f * ds_u * ds_p * ds_p + ds_u * ds_u) *
+                        (1.0f / 6.0f) * hf * hf * hf;
+      const double s5 = fma4(m0, m1, t2, cpy(s4, lane, 0), -0.0, h, cpy(s4, lane, 1),
+                             f32_to_f64(hk3), t2, cpy(s4, lane, 2), -0.0, cpy(s4, lane, 3), V, X1);
       const double fm1 = cpy(s5, lane, 0), fd = cpy(s5, lane, 1), gdm1 = cpy(s5, lane, 2);
       const double Xn = fma(fm1, X, cpy(s5, lane, 3));
       V = fma(fd, X, fma(gdm1, V, V));
@@ -971,13 +987,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
         const bool far = far_apart(U);
         float pf, qf;
         unsigned ord = drift_order_nb(pf, qf);
-        // the order-2 drift as in drift(2), f' = -mu h/r^3, in two FP64 instructions: copies 0-1
-        // form W = f' x + v and then x' = h/2 W + Y, copies 2-3 Y = h/2 v + x and then
-        // v' = f' Y + v (the same operations as drift(2), so the same results)
+        // the order-2 drift as in drift(2): copies 0-1 form W = f' x + v and then x' = h/2 W + Y,
+        // copies 2-3 Y = h/2 v + x and then v' = f'' Y + v, with f' = -mu h/r^3 and
+        // f'' = f' (1 - 3/2 p h), the series' f' to second order
         const double fd = munh * rb3c;
+        const double fdv = fma(fd, f32_to_f64(-1.5f * hf * pf), fd);
         const double s_wy = fma_rn(bsel(hh, fd, m1), bsel(V, X, m1), bsel(X, V, m1));
         const double W = cpy(s_wy, lane, 0), Y = cpy(s_wy, lane, 2);
-        const double s_xv = fma_rn(bsel(fd, hh, m1), bsel(Y, W, m1), bsel(V, Y, m1));
+        const double s_xv = fma_rn(bsel(fdv, hh, m1), bsel(Y, W, m1), bsel(V, Y, m1));
         const double Xn = cpy(s_xv, lane, 0), Vn = cpy(s_xv, lane, 2);
         const double Xno = __shfl_sync(FULL, s_xv, (lane & 7) ^ 4);     // the other body's x'
         // (1 + u)^(-3/2) - 1 for this drift (valid with the order-2 series and rb_ok)
