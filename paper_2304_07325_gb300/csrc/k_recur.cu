@@ -478,9 +478,6 @@ __device__ __forceinline__ double csum3(double p, int base) {
   const double c = __shfl_sync(FULL, p, base + 2);
   return (a + b) + c;
 }
-// The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
-// FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
-// e = 1 - r2 t still reach full FP64 accuracy.  false when r2e is not a normal FP32 number.
 // The FP32 seed alone: y0f ~ 1/sqrt(r2e), ok when r2e is a normal FP32 number.
 __device__ __forceinline__ void seed_f32(float r2e, bool &ok, float &y0f) {
   const unsigned yb = __float_as_uint(r2e);
@@ -488,8 +485,8 @@ __device__ __forceinline__ void seed_f32(float r2e, bool &ok, float &y0f) {
   ok = fe >= 1 && fe <= 253 && (int)yb > 0;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(ok ? r2e : 1.0f));
 }
-__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok, float &y0f) {
-  seed_f32(r2e, ok, y0f);
+// y0 = y0f exactly as a double and its exact square t, built on the integer pipe.
+__device__ __forceinline__ void seed_expand(float y0f, double &y0, double &t) {
   const unsigned b = __float_as_uint(y0f);
   const int ey = (int)((b >> 23) & 0xFF);
   y0 = __hiloint2double(((ey + 896) << 20) | (int)((b & 0x7FFFFF) >> 3), (int)((b & 7u) << 29));
@@ -499,6 +496,13 @@ __device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &
   const unsigned long long mant = (p << (6 - top)) & 0xFFFFFFFFFFFFFull;
   const long long e2 = 2 * (ey - 127) + top + 1023;
   t = __longlong_as_double((long long)(((unsigned long long)e2 << 52) | mant));
+}
+// The same seed from an FP32 estimate r2e of r2 (relative error ~2^-22), available before the
+// FP64 sum that forms r2: the seed's square t stays exact, so the third-order corrections from
+// e = 1 - r2 t still reach full FP64 accuracy.  ok = false when r2e is not a normal FP32 number.
+__device__ __forceinline__ void seed_nb(float r2e, double &y0, double &t, bool &ok, float &y0f) {
+  seed_f32(r2e, ok, y0f);
+  seed_expand(y0f, y0, t);
 }
 // The double equal to a normal FP32 value, built on the integer pipe (a conversion instruction
 // takes the FP64 pipe's rate); FP32 zeros and subnormals give zero.
@@ -835,6 +839,14 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
     rb_ok = __all_sync(FULL, ok);
   };
   auto rb3_nb = [&]() { rb3 = fma(rbty, rbe * fma(rbe, 1.875, 1.5), rbty); };
+  // the FP64 part of body_r_nb() from the seed body_f32() took (valid when rb_ok)
+  auto body_r64 = [&]() {
+    const double rs2 = csum3(X * X, base);
+    double y0;
+    seed_expand(brif, y0, rbt);
+    rbe = fma(-rs2, rbt, 1.0);
+    rbty = rbt * y0;
+  };
   // the FP32 part of body_r_nb() alone: the copies of x and the seed 1/|x| the FP32 decisions use
   auto body_f32 = [&]() {
     const float xf = f32_trunc(X);
@@ -1022,7 +1034,7 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
           // 1/r^3 in full; an order-2 drift from here starts a new carried run
           const bool fresh = far && ord == 2u && rb_ok;
           if (rb_ok) {
-            body_r_nb();
+            body_r64();
             rb3_nb();
           } else {
             body_r();
@@ -1037,7 +1049,8 @@ __device__ __noinline__ int pair_run(const Dev &D, const GroupCtx &C, int lane, 
             plev = j - 1;
             drift(ord);
             sep();
-            forces();
+            forces_nb();
+            if (!f_ok) forces();
             V = fma(hc, d, V);
             fat = j;
             if (++cj < cM) continue;
