@@ -33,13 +33,13 @@ FLOPS_PER_PAIR_CHECK = 18
 # smsp__inst_executed_pipe_fp64.sum per k_recursion launch against the launches' per-path sub-step
 # counts over four steps of the N = 10,000 disk (residuals <= 1.1 %; profiles/k_recursion_fp64_fit.md).
 # A general sub-step of a large group covers every body and pair of the group.
-FP64_PER_PAIR_SUBSTEP = 21.84
-FP64_PER_GENERAL_SUBSTEP = 951.9
+FP64_PER_PAIR_SUBSTEP = 21.70
+FP64_PER_GENERAL_SUBSTEP = 936.0
 # The recursion of the bound-pair group the profiles use (bodies of the N = 10,000 disk, seed 1002)
 BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
 # DRAM read + write per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, N = 10,000, FP64)
 # of the current kernels; None until a capture of the current kernel is on record
-RECURSION_TRAFFIC_BYTES = 1490432 + 24320      # first step of the disk (profiles/k_recursion_fp64_fit.md)
+RECURSION_TRAFFIC_BYTES = 1987840 + 19968      # first step of the disk (profiles/k_recursion_fp64_fit.md)
 KICK_TRAFFIC_BYTES = ((1149184 + 0) + (879360 + 0)) / 2        # kick 1, kick 2 (profiles/k_trap_fp64_disk_N10000.md)
 # Step size at which the batched and served forms and the one-at-a-time form all keep the energy
 # error of every merger-free disk below 1e-10 (measured on the 64 batched disks: 5.7e-11 after 20
