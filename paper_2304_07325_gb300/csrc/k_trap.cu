@@ -71,7 +71,7 @@ __device__ __forceinline__ size_t part_col(int m, int k) { return (size_t)m * SY
 struct RowF64 {
   int pi;
   bool live, row;          // a live body; live and massive (a row of the trapezoid)
-  double x, y, z, gm;
+  double x, y, z, ngm;     // position and -G m of the row body
   float xf, yf, zf, vxf, vyf, vzf, lam, sig;   // kick 1: FP32 prefilter copies
   int gid;                 // kick 2: encounter group
   double ax, ay, az;       // carried across the macro-tile's column blocks
@@ -83,7 +83,8 @@ __device__ __forceinline__ void row_load_fp64(const Dev &D, const TileCtx &c, in
   const int li = r.pi - c.off;
   r.live = li < c.n && D.alive[r.pi];
   r.row = r.live && li < c.nm;
-  r.x = D.x[r.pi]; r.y = D.y[r.pi]; r.z = D.z[r.pi]; r.gm = D.gm[r.pi];
+  r.x = D.x[r.pi]; r.y = D.y[r.pi]; r.z = D.z[r.pi];
+  r.ngm = __longlong_as_double(__double_as_longlong(D.gm[r.pi]) ^ (long long)0x8000000000000000ull);
   r.xf = r.yf = r.zf = r.vxf = r.vyf = r.vzf = r.lam = r.sig = 0.f;
   r.gid = -1;
   if (MODE == 1) {
@@ -152,7 +153,7 @@ __device__ __forceinline__ void tile_sweep_fp64(const Dev &D, const TileCtx &c, 
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     const double r3 = rinv3(r2);
     double sj = gmj * r3;
-    double si = r.gm * r3;
+    double si = r.ngm * r3;             // the column side's -G m_i / r^3
     if (MODE == 1) {
       const float dxf = xfj - r.xf, dyf = yfj - r.yf, dzf = zfj - r.zf;
       const float r2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
@@ -195,7 +196,7 @@ __device__ __forceinline__ void tile_sweep_fp64(const Dev &D, const TileCtx &c, 
     sj = keep_or_zero(sj, valid);
     si = keep_or_zero(si, valid);
     r.ax = fma(sj, dx, r.ax); r.ay = fma(sj, dy, r.ay); r.az = fma(sj, dz, r.az);
-    axj = fma(-si, dx, axj); ayj = fma(-si, dy, ayj); azj = fma(-si, dz, azj);
+    axj = fma(si, dx, axj); ayj = fma(si, dy, ayj); azj = fma(si, dz, azj);
     if (!diag || s + 1 < nsteps) rotate();
   }
   if (diag) {
