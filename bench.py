@@ -669,8 +669,8 @@ def run_ours(args):
         if not args.no_cpu_baseline and world == 1:
             cb, _, _ = cpu_baseline(args, d, P, args.cpu_budget_s)
         chain = chain_vs_cpu(sy, disk) if world == 1 and not args.no_cpu_baseline else None
-        # the batched and served forms against one simulation per launch, at matched energy error
-        # sequence, FP64, at a step size where every form keeps the energy error <= 1e-10
+        # the batched and served forms against one simulation per launch sequence, FP64, at a
+        # step size where every form keeps the energy error <= 1e-10
         batched = None if args.no_batched or world > 1 else bench_batched(sy, disk, args.batched_steps, 1, 2)
         served = None if args.no_served or world > 1 else bench_served(sy, args.served_requests,
                                                                           args.served_steps_cap)
