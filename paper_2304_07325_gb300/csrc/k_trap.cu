@@ -97,51 +97,65 @@ __device__ __forceinline__ void row_load_fp64(const Dev &D, const TileCtx &c, in
   r.ax = r.ay = r.az = 0.0;
 }
 
+// One warp's copy of a tile's 32 column bodies in shared memory.
+struct JStage {
+  double2 xy[32], zg[32];   // x, y | z, G m
+  float4 fa[32], fb[32];    // kick 1: the FP32 copies xf, yf, zf, vxf | vyf, vzf, lambda, sigma
+  int gid[32];              // kick 2: encounter group
+};
+
 // One 32 x 32 tile (rows of block I, columns of block J >= I): both reactions of every pair;
 // the row side goes into r.ax.., the column side comes back in cx, cy, cz (zero on a diagonal
-// tile, whose column side is folded into its rows).
+// tile, whose column side is folded into its rows).  The column bodies are staged in js once;
+// at step s lane l takes column (l + s + o) mod 32 (o = 1 on a diagonal tile), whose column-side
+// sums travel with it from lane to lane.
 template <int MODE>
 __device__ __forceinline__ void tile_sweep_fp64(const Dev &D, const TileCtx &c, int sys, RowF64 &r,
-                                                int I, int J, int lane, double &cx, double &cy, double &cz) {
+                                                int I, int J, int lane, JStage *js, double &cx,
+                                                double &cy, double &cz) {
   const bool diag = I == J;
-  int jid = J * 32 + lane;
-  const int lj0 = jid - c.off;
-  const bool live_j0 = lj0 < c.n && D.alive[jid];
-  int jflags = (live_j0 ? 1 : 0) | ((live_j0 && lj0 < c.nm) ? 2 : 0);
-  double xj = D.x[jid], yj = D.y[jid], zj = D.z[jid], gmj = D.gm[jid];
-  double axj = 0.0, ayj = 0.0, azj = 0.0;
-  float xfj = 0.f, yfj = 0.f, zfj = 0.f, vxfj = 0.f, vyfj = 0.f, vzfj = 0.f, lamj = 0.f, sigj = 0.f;
-  int gidj = -1;
-  if (MODE == 1) {
-    xfj = D.xf[jid]; yfj = D.yf[jid]; zfj = D.zf[jid];
-    vxfj = D.vxf[jid]; vyfj = D.vyf[jid]; vzfj = D.vzf[jid];
-    lamj = D.lamf[jid]; sigj = D.sigf[jid];
-  } else {
-    gidj = D.gid[jid];
+  {
+    const int j0 = J * 32 + lane;
+    __syncwarp();                         // the last tile's reads of js are done
+    js->xy[lane] = make_double2(D.x[j0], D.y[j0]);
+    js->zg[lane] = make_double2(D.z[j0], D.gm[j0]);
+    if (MODE == 1) {
+      js->fa[lane] = make_float4(D.xf[j0], D.yf[j0], D.zf[j0], D.vxf[j0]);
+      js->fb[lane] = make_float4(D.vyf[j0], D.vzf[j0], D.lamf[j0], D.sigf[j0]);
+    } else {
+      js->gid[lane] = D.gid[j0];
+    }
   }
+  const int lj0 = J * 32 + lane - c.off;
+  const bool live_j0 = lj0 < c.n && D.alive[J * 32 + lane];
+  const unsigned mlive = __ballot_sync(FULL, live_j0), mmass = __ballot_sync(FULL, live_j0 && lj0 < c.nm);
+  __syncwarp();
+  double axj = 0.0, ayj = 0.0, azj = 0.0;
   const float tauf = __double2float_ru(c.dt);
 
   auto rotate = [&]() {
     const int src = (lane + 1) & 31;
-    xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
-    zj = __shfl_sync(FULL, zj, src); gmj = __shfl_sync(FULL, gmj, src);
     axj = __shfl_sync(FULL, axj, src); ayj = __shfl_sync(FULL, ayj, src);
     azj = __shfl_sync(FULL, azj, src);
-    jid = __shfl_sync(FULL, jid, src); jflags = __shfl_sync(FULL, jflags, src);
-    if (MODE == 1) {
-      xfj = __shfl_sync(FULL, xfj, src); yfj = __shfl_sync(FULL, yfj, src);
-      zfj = __shfl_sync(FULL, zfj, src); vxfj = __shfl_sync(FULL, vxfj, src);
-      vyfj = __shfl_sync(FULL, vyfj, src); vzfj = __shfl_sync(FULL, vzfj, src);
-      lamj = __shfl_sync(FULL, lamj, src); sigj = __shfl_sync(FULL, sigj, src);
-    } else {
-      gidj = __shfl_sync(FULL, gidj, src);
-    }
   };
 
-  const int nsteps = diag ? 16 : 32;
-  if (diag) rotate();
+  const int nsteps = diag ? 16 : 32, o = diag ? 1 : 0;
 #pragma unroll 1
   for (int s = 0; s < nsteps; ++s) {
+    const int cj = (lane + s + o) & 31;
+    const int jid = J * 32 + cj;
+    const int jflags = (int)((mlive >> cj) & 1u) | (int)(((mmass >> cj) & 1u) << 1);
+    const double2 q0 = js->xy[cj], q1 = js->zg[cj];
+    const double xj = q0.x, yj = q0.y, zj = q1.x, gmj = q1.y;
+    float xfj = 0.f, yfj = 0.f, zfj = 0.f, vxfj = 0.f, vyfj = 0.f, vzfj = 0.f, lamj = 0.f, sigj = 0.f;
+    int gidj = -1;
+    if (MODE == 1) {
+      const float4 fa = js->fa[cj], fb = js->fb[cj];
+      xfj = fa.x; yfj = fa.y; zfj = fa.z; vxfj = fa.w;
+      vyfj = fb.x; vzfj = fb.y; lamj = fb.z; sigj = fb.w;
+    } else {
+      gidj = js->gid[cj];
+    }
     bool valid;
     if (!diag) {
       valid = r.row && (jflags & 1);
@@ -374,6 +388,7 @@ __device__ __forceinline__ void tile_sweep_mixed(const Dev &D, const TileCtx &c,
 template <int MODE>
 __global__ void __launch_bounds__(128) k_trap_fp64(Dev D) {
   __shared__ double colbuf[4][MC][3][32];     // [warp][column block][component][lane]
+  __shared__ JStage jstage[4];
   __shared__ int s_item;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nmac = D.ntiles_total;
@@ -395,7 +410,8 @@ __global__ void __launch_bounds__(128) k_trap_fp64(Dev D) {
       for (int k = 0; k < MC; ++k) {
         const int J = mt.z + k;
         double cx = 0.0, cy = 0.0, cz = 0.0;
-        if (has_row && J < mt.w && J >= I) tile_sweep_fp64<MODE>(D, c, mt.x, r, I, J, lane, cx, cy, cz);
+        if (has_row && J < mt.w && J >= I)
+          tile_sweep_fp64<MODE>(D, c, mt.x, r, I, J, lane, &jstage[w], cx, cy, cz);
         colbuf[w][k][0][lane] = cx; colbuf[w][k][1][lane] = cy; colbuf[w][k][2][lane] = cz;
       }
       double *rowp = D.part + part_row(m, w) + lane;
