@@ -10,10 +10,11 @@
 // rectangle, done by a work queue instead of index arithmetic).
 //
 // One CTA per macro-tile, one warp per row block: warp w keeps row particle (4q + w)*32 + l in
-// lane l and sweeps the macro's column blocks in turn; in each tile the column particles
-// rotate through the lanes with warp shuffles (32 steps; 16 on a diagonal tile, where each
-// unordered pair is met once), each carrying its own accumulator, so after the sweep every
-// column accumulator is back in its home lane.  The row accumulators run on across the
+// lane l and sweeps the macro's column blocks in turn; in each tile lane l meets column
+// (l + s) mod 32 at step s (32 steps; 16 on a diagonal tile, where each unordered pair is met
+// once).  In the FP64 path the tile's column bodies are staged in the warp's shared memory and
+// only their accumulators rotate through the lanes by warp shuffle; the mixed path rotates the
+// bodies with them.  After the sweep every column accumulator is back in its home lane.  The row accumulators run on across the
 // macro-tile's tiles and are written once per macro-tile; the four warps' column accumulators of
 // each column block are added in shared memory in warp order and written once.  Both kinds of partials are
 // summed later in a fixed order: the result does not depend on scheduling, on how many
