@@ -40,7 +40,7 @@ BOUND_PAIR_GROUP = [1244, 3406, 4643, 5122, 9870]
 # DRAM read + write per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, N = 10,000, FP64)
 # of the current kernels; None until a capture of the current kernel is on record
 RECURSION_TRAFFIC_BYTES = 1987840 + 19968      # first step of the disk (profiles/k_recursion_fp64_fit.md)
-KICK_TRAFFIC_BYTES = ((1149696 + 0) + (725248 + 0)) / 2        # kick 1, kick 2 (profiles/k_trap_fp64_disk_N10000.md)
+KICK_TRAFFIC_BYTES = ((1148928 + 0) + (725248 + 256)) / 2        # kick 1, kick 2 (profiles/k_trap_fp64_disk_N10000.md)
 # Step size at which the batched and served forms and the one-at-a-time form all keep the energy
 # error of every merger-free disk below 1e-10 (measured on the 64 batched disks: 5.7e-11 after 20
 # steps at 0.125 yr, 1.1e-10 at 0.2, 5.2e-10 at 0.5)
